@@ -1,0 +1,212 @@
+/*
+ * qarray.h -- C ABI of libqarray.so, the GB300 (sm_103a) implementation of the
+ * constant-capacitance-model ground-state method of "QArray" (arXiv 2404.04994).
+ *
+ * Problem (Sec. II): for dot-dot Maxwell block Cdd (N x N, symmetric positive
+ * definite), gate-dot block Cgd (N x N_g) and gate voltages V, the charge
+ * state of an open array is
+ *     n* = argmin_{n in Z^N, n >= 0} U(n),  U(n) = 1/2 (n - c)^T Cdd^-1 (n - c),
+ *     c = s * Cgd V   (s = +1, or -1 for the opposite carrier sign, Sec. II),
+ * (Eq. "free_energy" plus the n-independent constant 1/2 c^T Cdd^-1 c), and a
+ * closed array adds sum(n) = N_hat (constraint iii).  The method (Sec. III):
+ * continuous minimum of the relaxed problem (analytic, else a QP with x >= 0),
+ * then the argmin over the floor/floor+1 neighbours of that minimum, pruned by
+ * the threshold t of Eq. "threshold" (t = 1 is the default algorithm, t < 1
+ * the thresholded algorithm; a closed array whose pruned set holds no state
+ * with the right total doubles t per pixel).
+ *
+ * Conventions shared by every call:
+ *  - Return value: QA_OK (0) or a negative QA_ERR_* code; the message of the
+ *    last failure on the calling thread is qa_last_error().  No call throws.
+ *  - Host pointers are read during the call and never retained.  Device
+ *    pointers (suffix _dev, or documented as device) must stay valid until the
+ *    work enqueued on `stream` has completed; they are never freed here.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued asynchronously; errors detected on the host are returned
+ *    before anything is enqueued.  Calls that share one model must not overlap
+ *    on the GPU (the model owns one scratch workspace); use one model per
+ *    concurrent stream.
+ *  - Matrices are row-major FP64.  Charge maps are channel-last [H, W, N]
+ *    (pixel p = iy * W + ix), the (100, 100, 2) layout of Sec. V.
+ *  - Every call runs on the device that was current at qa_model_create.
+ */
+#ifndef QARRAY_H
+#define QARRAY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QA_MAX_DOT 16
+#define QA_MAX_GATE 64
+
+enum {
+    QA_OK = 0,
+    QA_ERR_INVALID = -1,       /* null pointer, NaN/Inf input, bad enum      */
+    QA_ERR_SHAPE = -2,         /* n_dot / n_gate / raster size out of range  */
+    QA_ERR_NOT_SYMMETRIC = -3, /* |Cdd - Cdd^T| > 1e-12 max|Cdd|             */
+    QA_ERR_NOT_PD = -4,        /* Cholesky of Cdd failed (Appendix B)         */
+    QA_ERR_RANGE = -5,         /* threshold outside [0, 1], kT <= 0, N_hat<0  */
+    QA_ERR_OVERFLOW = -6,      /* a charge does not fit the output type       */
+    QA_ERR_CUDA = -7,          /* a CUDA runtime call failed                  */
+    QA_ERR_TIMEOUT = -8,       /* a bounded device wait expired               */
+    QA_ERR_NOMEM = -9,         /* workspace allocation failed                 */
+    QA_ERR_UNRESOLVED = -10    /* a pixel the FP64 recheck could not settle   */
+};
+
+/* Input form of the capacitances (Sec. V, DotArray keyword arguments). */
+enum {
+    QA_FORM_MAXWELL = 0,  /* cdd, cgd: Maxwell blocks (lower-case in the paper) */
+    QA_FORM_COUPLING = 1  /* Cdd, Cgd: non-negative couplings (upper-case);
+                             converted by Appendix B: cdd_ii = sum of dot i's
+                             couplings to dots and gates, cdd_ij = -C_ij,
+                             cgd = Cgd (gate couplings are the induced charge
+                             per volt). */
+};
+
+/* Per-pixel status bits written to out_flags (uint8 per pixel). */
+enum {
+    QA_FLAG_NEAR_TIE = 1,    /* FP32 best/runner-up gap under the error bound */
+    QA_FLAG_BOUNDARY = 2,    /* continuous minimum within the error bound of a
+                                floor or threshold decision                   */
+    QA_FLAG_QP = 4,          /* analytic minimum infeasible: QP was solved    */
+    QA_FLAG_QP_CAP = 8,      /* FP32 active-set iteration hit its cap          */
+    QA_FLAG_RECHECKED = 16,  /* pixel re-evaluated in FP64                     */
+    QA_FLAG_DOUBLED = 32,    /* closed threshold doubled at least once         */
+    QA_FLAG_UNRESOLVED = 64, /* FP64 recheck could not settle the pixel        */
+    QA_FLAG_OVERFLOW = 128   /* a charge exceeds the int8 output               */
+};
+
+typedef struct qa_model qa_model;
+
+/* A 2-D gate-voltage raster (the meshgrid of Sec. V, with arbitrary virtual
+ * gate directions):  V(ix, iy) = V0 + xs[ix] u + ys[iy] w,
+ * xs = linspace(x0, x1, W), ys = linspace(y0, y1, H).  V0, u, w are HOST
+ * arrays of length n_gate.  1 <= W, H and W * H <= 2^31 - 1. */
+typedef struct {
+    const double* V0;
+    const double* u;
+    const double* w;
+    double x0, x1, y0, y1;
+    int W, H;
+} qa_raster;
+
+/* Counters of the last ground-state / soft call on a model (read back with a
+ * stream synchronisation by qa_model_stats). */
+typedef struct {
+    long long pixels;          /* pixels processed                            */
+    long long candidates;      /* admissible candidates (2^k or C(k, w))      */
+    long long evaluated;       /* candidate energies evaluated by the kernels */
+    long long qp_pixels;       /* pixels that needed the QP                   */
+    long long flagged;         /* pixels queued for the FP64 recheck          */
+    long long near_tie;        /* ... because of the top-two gap              */
+    long long boundary;        /* ... because of a decision boundary / QP cap */
+    long long unresolved;      /* pixels the recheck could not settle         */
+    long long overflow;        /* pixels whose charges exceed int8            */
+    long long doubled;         /* closed pixels whose threshold was doubled   */
+    long long shortlist_max;   /* largest FP64 shortlist in the recheck       */
+    int team;                  /* lanes per pixel used by the search kernel   */
+    int inner_bits;            /* unrolled inner / middle bits of the search  */
+    int middle_bits;
+} qa_stats;
+
+/* Create a model from HOST matrices Cdd [n_dot x n_dot] and Cgd
+ * [n_dot x n_gate] (copied).  Validates 1 <= n_dot <= 16, 1 <= n_gate <= 64,
+ * finiteness, symmetry and positive definiteness (Appendix B; Sec. V
+ * validation), computes M = Cdd^-1 in FP64 and uploads the model to the
+ * current device.  carrier_sign = +1 (c = Cgd V) or -1 (c = -Cgd V, Q = +-eN,
+ * Sec. II).  *out receives a handle owned by the caller (qa_model_destroy).
+ * Errors: QA_ERR_INVALID, QA_ERR_SHAPE, QA_ERR_NOT_SYMMETRIC, QA_ERR_NOT_PD,
+ * QA_ERR_CUDA, QA_ERR_NOMEM. */
+int qa_model_create(const double* Cdd, const double* Cgd, int n_dot, int n_gate,
+                    int form, double carrier_sign, qa_model** out);
+
+/* Replace the capacitances of a model from HOST matrices (same shape and form
+ * as at creation); same checks as qa_model_create.  Synchronous. */
+int qa_model_update(qa_model* m, const double* Cdd, const double* Cgd);
+
+/* Replace the capacitances from DEVICE FP64 Maxwell matrices (same shape) and
+ * recompute M = Cdd^-1 by an FP64 Cholesky on the GPU, asynchronously on
+ * `stream`.  A Cholesky failure is recorded on the device; the next call that
+ * reads the model on that stream writes QA_FLAG_UNRESOLVED for every pixel and
+ * qa_model_stats reports it (host checks are impossible without a sync).
+ * Used by the capacitance-fitting loop. */
+int qa_model_update_dev(qa_model* m, const double* Cdd_dev,
+                        const double* Cgd_dev, void* stream);
+
+/* Release the model and its device memory (synchronises the device). */
+int qa_model_destroy(qa_model* m);
+
+/* Shape of a model: *n_dot, *n_gate (either may be NULL). */
+int qa_model_shape(const qa_model* m, int* n_dot, int* n_gate);
+
+/* Copy the model's current FP64 Cdd, M = Cdd^-1 and Cgd to HOST arrays (any
+ * may be NULL); synchronises the device. */
+int qa_model_get(const qa_model* m, double* Cdd, double* M, double* Cgd);
+
+/* Ground state of an OPEN array on every raster pixel (Sec. III, constraints
+ * i-ii).  threshold t in [0, 1] (Eq. "threshold"; 1 = default algorithm).
+ * DEVICE outputs, caller-owned:
+ *   out_n     int8  [H, W, n_dot]  charge configuration n*;
+ *   out_U     FP64  [H, W]         U(n*) (nullable);
+ *   out_flags uint8 [H, W]         QA_FLAG_* bits (nullable).
+ * Errors: QA_ERR_INVALID, QA_ERR_SHAPE, QA_ERR_RANGE, QA_ERR_CUDA,
+ * QA_ERR_NOMEM.  Charges above 127 saturate and set QA_FLAG_OVERFLOW. */
+int qa_ground_state_open(qa_model* m, const qa_raster* r, double threshold,
+                         int8_t* out_n, double* out_U, uint8_t* out_flags,
+                         void* stream);
+
+/* Ground state of a CLOSED array holding n_charges carriers (constraint iii;
+ * Appendix D continuous minimum; per-pixel threshold doubling of Sec. III.B).
+ * Outputs as qa_ground_state_open.  n_charges >= 0, else QA_ERR_RANGE. */
+int qa_ground_state_closed(qa_model* m, const qa_raster* r, double threshold,
+                           int n_charges, int8_t* out_n, double* out_U,
+                           uint8_t* out_flags, void* stream);
+
+/* Ground state at an arbitrary list of P gate-voltage vectors V_dev (DEVICE,
+ * FP64 [P, n_gate]), the random-voltage workload of Sec. VII.  closed = 0/1.
+ * Outputs as above with H * W replaced by P. */
+int qa_ground_state_points(qa_model* m, const double* V_dev, long long P,
+                           double threshold, int closed, int n_charges,
+                           int8_t* out_n, double* out_U, uint8_t* out_flags,
+                           void* stream);
+
+/* Finite-temperature occupation (Sec. IV.B, Eq. "softargmin") over the
+ * method's candidate set at threshold t (closed: states with sum N_hat only):
+ *   <n> = sum_c n_c exp(-U_c / kT) / Z,  log Z = log sum_c exp(-U_c / kT),
+ * kT in the units of U (e^2 / Cdd_ii with Cdd_ii = 1).  DEVICE outputs:
+ * out_mean FP32 [H, W, n_dot], out_logZ FP32 [H, W] (nullable).
+ * kT > 0, else QA_ERR_RANGE. */
+int qa_soft_occupation(qa_model* m, const qa_raster* r, double kT,
+                       double threshold, int closed, int n_charges,
+                       float* out_mean, float* out_logZ, void* stream);
+
+/* Gradient of a loss L through qa_soft_occupation with the candidate set of
+ * every pixel frozen (the set is piecewise constant in the parameters).  The
+ * paper has no gradient (Sec. VI notes that its JAX core cannot
+ * differentiate); this follows from differentiating Eq. "softargmin":
+ *   a_c = -(w_c / kT) (g . n_c - g . <n>),  g = dL/d<n> of the pixel,
+ *   dL/dM   = 1/2 sum_p sum_c a_c r_c r_c^T,   r_c = n_c - c,
+ *   dL/dc_p = -M sum_c a_c r_c,   dL/dCgd = s sum_p dL/dc_p V_p^T,
+ *   dL/dCdd = -M (dL/dM) M.
+ * grad_mean: DEVICE FP32 [H, W, n_dot].  Outputs: DEVICE FP64 dL_dCdd
+ * [n_dot x n_dot] and dL_dCgd [n_dot x n_gate], overwritten (not
+ * accumulated).  The reduction over pixels is deterministic. */
+int qa_soft_occupation_backward(qa_model* m, const qa_raster* r, double kT,
+                                double threshold, int closed, int n_charges,
+                                const float* grad_mean, double* dL_dCdd,
+                                double* dL_dCgd, void* stream);
+
+/* Counters of the last call on this model; synchronises `stream` first. */
+int qa_model_stats(qa_model* m, void* stream, qa_stats* out);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* qa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,353 @@
+"""ctypes binding of libqarray.so (include/qarray.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Device buffers are torch CUDA tensors (PyTorch provides device
+memory and streams); host matrices are numpy arrays.  The library is built
+in-tree on first use if missing; when it cannot be loaded every call raises
+-- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_DOT = 16
+MAX_GATE = 64
+
+QA_OK = 0
+ERRORS = {
+    -1: "QA_ERR_INVALID", -2: "QA_ERR_SHAPE", -3: "QA_ERR_NOT_SYMMETRIC",
+    -4: "QA_ERR_NOT_PD", -5: "QA_ERR_RANGE", -6: "QA_ERR_OVERFLOW",
+    -7: "QA_ERR_CUDA", -8: "QA_ERR_TIMEOUT", -9: "QA_ERR_NOMEM",
+    -10: "QA_ERR_UNRESOLVED",
+}
+QA_FORM_MAXWELL = 0
+QA_FORM_COUPLING = 1
+
+FLAG_NEAR_TIE = 1
+FLAG_BOUNDARY = 2
+FLAG_QP = 4
+FLAG_QP_CAP = 8
+FLAG_RECHECKED = 16
+FLAG_DOUBLED = 32
+FLAG_UNRESOLVED = 64
+FLAG_OVERFLOW = 128
+
+
+class QAError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class qa_raster(ctypes.Structure):
+    _fields_ = [("V0", ctypes.POINTER(ctypes.c_double)),
+                ("u", ctypes.POINTER(ctypes.c_double)),
+                ("w", ctypes.POINTER(ctypes.c_double)),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("W", ctypes.c_int), ("H", ctypes.c_int)]
+
+
+class qa_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_longlong) for n in (
+        "pixels", "candidates", "evaluated", "qp_pixels", "flagged", "near_tie",
+        "boundary", "unresolved", "overflow", "doubled", "shortlist_max")] + [
+        ("team", ctypes.c_int), ("inner_bits", ctypes.c_int),
+        ("middle_bits", ctypes.c_int)]
+
+
+_lib = None
+_SYMBOLS = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load (building if needed) libqarray.so; raises if that fails."""
+    global _lib, _SYMBOLS
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    I = ctypes.c_int
+    sig = {
+        "qa_model_create": (I, [D, D, I, I, I, ctypes.c_double, ctypes.POINTER(P)]),
+        "qa_model_update": (I, [P, D, D]),
+        "qa_model_update_dev": (I, [P, P, P, P]),
+        "qa_model_destroy": (I, [P]),
+        "qa_model_shape": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "qa_model_get": (I, [P, D, D, D]),
+        "qa_ground_state_open": (I, [P, ctypes.POINTER(qa_raster), ctypes.c_double,
+                                     P, P, P, P]),
+        "qa_ground_state_closed": (I, [P, ctypes.POINTER(qa_raster), ctypes.c_double,
+                                       I, P, P, P, P]),
+        "qa_ground_state_points": (I, [P, P, ctypes.c_longlong, ctypes.c_double, I, I,
+                                       P, P, P, P]),
+        "qa_soft_occupation": (I, [P, ctypes.POINTER(qa_raster), ctypes.c_double,
+                                   ctypes.c_double, I, I, P, P, P]),
+        "qa_soft_occupation_backward": (I, [P, ctypes.POINTER(qa_raster),
+                                            ctypes.c_double, ctypes.c_double, I, I,
+                                            P, P, P, P]),
+        "qa_model_stats": (I, [P, P, ctypes.POINTER(qa_stats)]),
+        "qa_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _SYMBOLS = tuple(sig)
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    load()
+    return _SYMBOLS
+
+
+def qa_last_error() -> str:
+    return load().qa_last_error().decode()
+
+
+def _check(rc):
+    if rc != QA_OK:
+        raise QAError(rc, qa_last_error())
+
+
+def _host(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype, numel=None, name="buffer"):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_raster(r, n_gate):
+    """qa_raster from a dict {V0, u, w, x0, x1, y0, y1, W, H}; the struct
+    keeps its host arrays alive."""
+    V0, pV0 = _host(r["V0"], (n_gate,))
+    u, pu = _host(r["u"], (n_gate,))
+    w, pw = _host(r["w"], (n_gate,))
+    s = qa_raster(pV0, pu, pw, float(r["x0"]), float(r["x1"]), float(r["y0"]),
+                  float(r["y1"]), int(r["W"]), int(r["H"]))
+    s._keep = (V0, u, w)
+    return s
+
+
+# --------------------------------------------------------------------------
+# the C ABI, name for name
+# --------------------------------------------------------------------------
+
+def qa_model_create(Cdd, Cgd, form=QA_FORM_MAXWELL, carrier_sign=1.0):
+    Cgd = np.atleast_2d(np.asarray(Cgd, dtype=np.float64))
+    n, ng = Cgd.shape
+    Cd, pCd = _host(Cdd, (n, n))
+    Cg, pCg = _host(Cgd, (n, ng))
+    h = ctypes.c_void_p()
+    _check(load().qa_model_create(pCd, pCg, n, ng, int(form), float(carrier_sign),
+                                  ctypes.byref(h)))
+    return h
+
+
+def qa_model_update(m, Cdd, Cgd):
+    n, ng = qa_model_shape(m)
+    _, pCd = _host(Cdd, (n, n))
+    _, pCg = _host(Cgd, (n, ng))
+    _check(load().qa_model_update(m, pCd, pCg))
+
+
+def qa_model_update_dev(m, Cdd_dev, Cgd_dev, stream=None):
+    import torch
+    n, ng = qa_model_shape(m)
+    _check(load().qa_model_update_dev(m, _dev(Cdd_dev, torch.float64, n * n, "Cdd"),
+                                      _dev(Cgd_dev, torch.float64, n * ng, "Cgd"),
+                                      _stream(stream)))
+
+
+def qa_model_destroy(m):
+    _check(load().qa_model_destroy(m))
+
+
+def qa_model_shape(m):
+    n = ctypes.c_int()
+    ng = ctypes.c_int()
+    _check(load().qa_model_shape(m, ctypes.byref(n), ctypes.byref(ng)))
+    return n.value, ng.value
+
+
+def qa_model_get(m):
+    n, ng = qa_model_shape(m)
+    Cdd = np.zeros((n, n))
+    M = np.zeros((n, n))
+    Cgd = np.zeros((n, ng))
+    D = ctypes.POINTER(ctypes.c_double)
+    _check(load().qa_model_get(m, Cdd.ctypes.data_as(D), M.ctypes.data_as(D),
+                               Cgd.ctypes.data_as(D)))
+    return Cdd, M, Cgd
+
+
+def qa_ground_state_open(m, raster, threshold, out_n, out_U=None, out_flags=None,
+                         stream=None):
+    import torch
+    n, ng = qa_model_shape(m)
+    r = make_raster(raster, ng)
+    P = r.W * r.H
+    _check(load().qa_ground_state_open(
+        m, ctypes.byref(r), float(threshold), _dev(out_n, torch.int8, P * n, "out_n"),
+        _dev(out_U, torch.float64, P, "out_U"),
+        _dev(out_flags, torch.uint8, P, "out_flags"), _stream(stream)))
+
+
+def qa_ground_state_closed(m, raster, threshold, n_charges, out_n, out_U=None,
+                           out_flags=None, stream=None):
+    import torch
+    n, ng = qa_model_shape(m)
+    r = make_raster(raster, ng)
+    P = r.W * r.H
+    _check(load().qa_ground_state_closed(
+        m, ctypes.byref(r), float(threshold), int(n_charges),
+        _dev(out_n, torch.int8, P * n, "out_n"), _dev(out_U, torch.float64, P, "out_U"),
+        _dev(out_flags, torch.uint8, P, "out_flags"), _stream(stream)))
+
+
+def qa_ground_state_points(m, V, threshold, closed, n_charges, out_n, out_U=None,
+                           out_flags=None, stream=None):
+    import torch
+    n, ng = qa_model_shape(m)
+    P = V.shape[0]
+    _check(load().qa_ground_state_points(
+        m, _dev(V, torch.float64, P * ng, "V"), P, float(threshold), int(closed),
+        int(n_charges), _dev(out_n, torch.int8, P * n, "out_n"),
+        _dev(out_U, torch.float64, P, "out_U"),
+        _dev(out_flags, torch.uint8, P, "out_flags"), _stream(stream)))
+
+
+def qa_soft_occupation(m, raster, kT, threshold, closed, n_charges, out_mean,
+                       out_logZ=None, stream=None):
+    import torch
+    n, ng = qa_model_shape(m)
+    r = make_raster(raster, ng)
+    P = r.W * r.H
+    _check(load().qa_soft_occupation(
+        m, ctypes.byref(r), float(kT), float(threshold), int(closed), int(n_charges),
+        _dev(out_mean, torch.float32, P * n, "out_mean"),
+        _dev(out_logZ, torch.float32, P, "out_logZ"), _stream(stream)))
+
+
+def qa_soft_occupation_backward(m, raster, kT, threshold, closed, n_charges,
+                                grad_mean, dL_dCdd, dL_dCgd, stream=None):
+    import torch
+    n, ng = qa_model_shape(m)
+    r = make_raster(raster, ng)
+    P = r.W * r.H
+    _check(load().qa_soft_occupation_backward(
+        m, ctypes.byref(r), float(kT), float(threshold), int(closed), int(n_charges),
+        _dev(grad_mean, torch.float32, P * n, "grad_mean"),
+        _dev(dL_dCdd, torch.float64, n * n, "dL_dCdd"),
+        _dev(dL_dCgd, torch.float64, n * ng, "dL_dCgd"), _stream(stream)))
+
+
+def qa_model_stats(m, stream=None):
+    s = qa_stats()
+    _check(load().qa_model_stats(m, _stream(stream), ctypes.byref(s)))
+    return {f[0]: getattr(s, f[0]) for f in qa_stats._fields_}
+
+
+# --------------------------------------------------------------------------
+# convenience: a model object that allocates its outputs as torch tensors
+# --------------------------------------------------------------------------
+
+class Model:
+    """Owns a qa_model handle; methods mirror the paper's DotArray calls
+    (Sec. V): ground_state_open / ground_state_closed / soft occupation."""
+
+    def __init__(self, Cdd, Cgd, form=QA_FORM_MAXWELL, carrier_sign=1.0):
+        self.handle = qa_model_create(Cdd, Cgd, form, carrier_sign)
+        self.n_dot, self.n_gate = qa_model_shape(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            qa_model_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _outs(self, P, energies, flags):
+        import torch
+        n = torch.empty((P, self.n_dot), dtype=torch.int8, device="cuda")
+        U = torch.empty(P, dtype=torch.float64, device="cuda") if energies else None
+        f = torch.empty(P, dtype=torch.uint8, device="cuda") if flags else None
+        return n, U, f
+
+    def ground_state_open(self, raster, threshold=1.0, energies=True, flags=True,
+                          stream=None):
+        P = int(raster["W"]) * int(raster["H"])
+        n, U, f = self._outs(P, energies, flags)
+        qa_ground_state_open(self.handle, raster, threshold, n, U, f, stream)
+        return n.view(int(raster["H"]), int(raster["W"]), self.n_dot), U, f
+
+    def ground_state_closed(self, raster, n_charges, threshold=1.0, energies=True,
+                            flags=True, stream=None):
+        P = int(raster["W"]) * int(raster["H"])
+        n, U, f = self._outs(P, energies, flags)
+        qa_ground_state_closed(self.handle, raster, threshold, n_charges, n, U, f,
+                               stream)
+        return n.view(int(raster["H"]), int(raster["W"]), self.n_dot), U, f
+
+    def ground_state_points(self, V, threshold=1.0, closed=False, n_charges=0,
+                            energies=True, flags=True, stream=None):
+        P = int(V.shape[0])
+        n, U, f = self._outs(P, energies, flags)
+        qa_ground_state_points(self.handle, V, threshold, closed, n_charges, n, U, f,
+                               stream)
+        return n, U, f
+
+    def soft_occupation(self, raster, kT, threshold=1.0, closed=False, n_charges=0,
+                        stream=None):
+        import torch
+        P = int(raster["W"]) * int(raster["H"])
+        mean = torch.empty((P, self.n_dot), dtype=torch.float32, device="cuda")
+        logZ = torch.empty(P, dtype=torch.float32, device="cuda")
+        qa_soft_occupation(self.handle, raster, kT, threshold, closed, n_charges, mean,
+                           logZ, stream)
+        return mean, logZ
+
+    def stats(self, stream=None):
+        return qa_model_stats(self.handle, stream)

@@ -1,0 +1,547 @@
+// qa_api.cu -- host implementation of the C ABI declared in include/qarray.h.
+//
+// Argument validation, the FP64 model set-up (Cholesky inverse of Cdd,
+// Appendix B positive-definiteness check), workspace management and kernel
+// dispatch.  No pixel work happens on the host.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/qarray.h"
+#include "qa_launch.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(QA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool finite_all(const double* a, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+// Cholesky inverse in FP64; returns false if A is not positive definite.
+bool spd_inverse(int n, const double* A, double* Ainv) {
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double d = A[j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    L[j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double s = A[i * n + j];
+      for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+      L[i * n + j] = s / ljj;
+    }
+  }
+  for (int col = 0; col < n; ++col) {
+    std::vector<double> z(n), y(n);
+    for (int i = 0; i < n; ++i) {
+      double s = (i == col) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= L[i * n + k] * z[k];
+      z[i] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double s = z[i];
+      for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * y[k];
+      y[i] = s / L[i * n + i];
+    }
+    for (int i = 0; i < n; ++i) Ainv[i * n + col] = y[i];
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      const double s = 0.5 * (Ainv[i * n + j] + Ainv[j * n + i]);
+      Ainv[i * n + j] = Ainv[j * n + i] = s;
+    }
+  return true;
+}
+
+double norm1(int n, const double* A) {
+  double best = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += std::fabs(A[i * n + j]);
+    best = s > best ? s : best;
+  }
+  return best;
+}
+
+}  // namespace
+
+struct qa_model {
+  int n = 0, ng = 0, form = 0;
+  double carrier = 1.0;
+  int device = 0, num_sms = 0;
+  qa::ModelData host;            // host mirror (stale after update_dev)
+  bool host_stale = false;
+  qa::ModelData* d_md = nullptr; // device copy
+  void* ws = nullptr;            // workspace
+  size_t ws_bytes = 0;
+  qa::Counters* d_cnt = nullptr;
+  qa::SearchCfg last_cfg{0, 0, 0};
+  long long last_P = 0;
+};
+
+namespace {
+
+// Validate + convert host matrices into a ModelData (Maxwell form).
+int build_model(int n, int ng, int form, const double* Cdd_in,
+                const double* Cgd_in, qa::ModelData* md) {
+  if (!Cdd_in || !Cgd_in) return fail(QA_ERR_INVALID, "null capacitance matrix");
+  if (n < 1 || n > QA_MAX_DOT) return fail(QA_ERR_SHAPE, "n_dot=%d outside [1, %d]", n, QA_MAX_DOT);
+  if (ng < 1 || ng > QA_MAX_GATE) return fail(QA_ERR_SHAPE, "n_gate=%d outside [1, %d]", ng, QA_MAX_GATE);
+  if (!finite_all(Cdd_in, (size_t)n * n) || !finite_all(Cgd_in, (size_t)n * ng))
+    return fail(QA_ERR_INVALID, "non-finite capacitance");
+  std::memset(md, 0, sizeof(*md));
+  double amax = 0.0;
+  for (int e = 0; e < n * n; ++e) amax = std::fmax(amax, std::fabs(Cdd_in[e]));
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (std::fabs(Cdd_in[i * n + j] - Cdd_in[j * n + i]) > 1e-12 * amax)
+        return fail(QA_ERR_NOT_SYMMETRIC, "Cdd is not symmetric at (%d, %d)", i, j);
+  if (form == QA_FORM_MAXWELL) {
+    for (int e = 0; e < n * n; ++e) md->Cdd[e] = Cdd_in[e];
+  } else if (form == QA_FORM_COUPLING) {
+    // Appendix B: Maxwell diagonal = total capacitance of the node, off-
+    // diagonals = minus the coupling.
+    for (int i = 0; i < n; ++i) {
+      double tot = 0.0;
+      for (int j = 0; j < n; ++j) {
+        if (j == i) continue;
+        if (Cdd_in[i * n + j] < 0.0) return fail(QA_ERR_INVALID, "negative coupling Cdd[%d,%d]", i, j);
+        tot += Cdd_in[i * n + j];
+        md->Cdd[i * n + j] = -Cdd_in[i * n + j];
+      }
+      for (int g = 0; g < ng; ++g) {
+        if (Cgd_in[i * ng + g] < 0.0) return fail(QA_ERR_INVALID, "negative coupling Cgd[%d,%d]", i, g);
+        tot += Cgd_in[i * ng + g];
+      }
+      md->Cdd[i * n + i] = tot;
+    }
+  } else {
+    return fail(QA_ERR_INVALID, "unknown form %d", form);
+  }
+  for (int e = 0; e < n * ng; ++e) md->Cgd[e] = Cgd_in[e];
+  if (!spd_inverse(n, md->Cdd, md->M))
+    return fail(QA_ERR_NOT_PD, "Cdd is not positive definite");
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double r = 0.0;
+    for (int j = 0; j < n; ++j) r += md->Cdd[i * n + j];
+    md->vs[i] = r;
+    s += r;
+  }
+  if (!(s > 0.0)) return fail(QA_ERR_NOT_PD, "1^T Cdd 1 <= 0");
+  for (int i = 0; i < n; ++i) md->vs[i] /= s;
+  md->cond = norm1(n, md->Cdd) * norm1(n, md->M);
+  md->status = 0;
+  return QA_OK;
+}
+
+int ensure_workspace(qa_model* m, size_t bytes) {
+  if (bytes <= m->ws_bytes) return QA_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  if (m->ws) cudaFree(m->ws);
+  m->ws = nullptr;
+  m->ws_bytes = 0;
+  const size_t want = bytes + bytes / 2 + (1u << 20);
+  e = cudaMalloc(&m->ws, want);
+  if (e != cudaSuccess) return fail(QA_ERR_NOMEM, "workspace of %zu bytes: %s", want, cudaGetErrorString(e));
+  m->ws_bytes = want;
+  return QA_OK;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Device id check: every call runs on the model's device.
+int select_device(const qa_model* m) {
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != m->device) {
+    e = cudaSetDevice(m->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  }
+  return QA_OK;
+}
+
+qa::SearchCfg choose_cfg(int n, double t, long long P, int num_sms) {
+  const double kexp = (t >= 1.0) ? (double)n : (double)n * std::log2(1.0 + t);
+  const int ke = (int)std::ceil(kexp - 1e-9);
+  qa::SearchCfg c;
+  if (n <= 2) c = {2, 0, 1};
+  else if (ke <= 4) c = {4, 0, 1};
+  else if (ke <= 7) c = {4, 3, 1};
+  else {
+    c = {5, 4, 1};
+    const int rest = ke - 9;
+    c.T = rest <= 0 ? 1 : (rest >= 5 ? 32 : (1 << rest));
+  }
+  // spread a small raster over more lanes while each lane keeps >= 2 outer
+  // states of work
+  const int spare = ke - c.L1 - c.L2;
+  while (c.T < 32 && P * c.T < (long long)num_sms * 128 * 4 && spare > 0 &&
+         (1 << spare) >= 4 * c.T)
+    c.T *= 2;
+  return c;
+}
+
+struct ScanIn {
+  const qa_raster* r = nullptr;
+  const double* V = nullptr;
+  long long P = 0;
+};
+
+int make_scan(const qa_model* m, const ScanIn& in, qa::Scan* sc) {
+  std::memset(sc, 0, sizeof(*sc));
+  if (in.r) {
+    const qa_raster* r = in.r;
+    if (!r->V0 || !r->u || !r->w) return fail(QA_ERR_INVALID, "raster vectors must be non-null");
+    if (r->W < 1 || r->H < 1 || (long long)r->W * r->H > 2147483647LL)
+      return fail(QA_ERR_SHAPE, "raster %d x %d out of range", r->W, r->H);
+    if (!std::isfinite(r->x0) || !std::isfinite(r->x1) || !std::isfinite(r->y0) ||
+        !std::isfinite(r->y1) || !finite_all(r->V0, m->ng) || !finite_all(r->u, m->ng) ||
+        !finite_all(r->w, m->ng))
+      return fail(QA_ERR_INVALID, "non-finite raster");
+    sc->kind = 0;
+    sc->W = r->W;
+    sc->H = r->H;
+    sc->P = (long long)r->W * r->H;
+    sc->x0 = r->x0;
+    sc->dx = r->W > 1 ? (r->x1 - r->x0) / (double)(r->W - 1) : 0.0;
+    sc->y0 = r->y0;
+    sc->dy = r->H > 1 ? (r->y1 - r->y0) / (double)(r->H - 1) : 0.0;
+    for (int g = 0; g < m->ng; ++g) {
+      sc->V0[g] = r->V0[g];
+      sc->u[g] = r->u[g];
+      sc->w[g] = r->w[g];
+    }
+  } else {
+    if (in.P < 0 || in.P > 2147483647LL) return fail(QA_ERR_SHAPE, "P=%lld out of range", in.P);
+    if (in.P > 0 && !in.V) return fail(QA_ERR_INVALID, "null voltage list");
+    sc->kind = 1;
+    sc->P = in.P;
+    sc->V = in.V;
+  }
+  return QA_OK;
+}
+
+int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
+                     int n_charges, int8_t* out_n, double* out_U,
+                     uint8_t* out_flags, void* stream) {
+  if (!m) return fail(QA_ERR_INVALID, "null model");
+  if (!(t >= 0.0 && t <= 1.0)) return fail(QA_ERR_RANGE, "threshold %g outside [0, 1]", t);
+  if (closed && (n_charges < 0 || n_charges > 100000))
+    return fail(QA_ERR_RANGE, "n_charges=%d out of range", n_charges);
+  qa::Scan sc;
+  int rc = make_scan(m, in, &sc);
+  if (rc) return rc;
+  if (sc.P > 0 && !out_n) return fail(QA_ERR_INVALID, "null out_n");
+  if ((rc = select_device(m))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long P = sc.P;
+  const size_t off_list = align_up(sizeof(qa::Counters), 256);
+  const size_t off_recs = align_up(off_list + sizeof(int) * (size_t)(P > 0 ? P : 1), 256);
+  const size_t total = off_recs + sizeof(qa::PixRec) * (size_t)(P > 0 ? P : 1);
+  if ((rc = ensure_workspace(m, total))) return rc;
+  char* ws = (char*)m->ws;
+  m->d_cnt = (qa::Counters*)ws;
+  cudaError_t e = cudaMemsetAsync(m->d_cnt, 0, sizeof(qa::Counters), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  m->last_P = P;
+  if (P == 0) return QA_OK;
+
+  qa::GsLaunch a;
+  std::memset(&a, 0, sizeof(a));
+  a.md = m->d_md;
+  a.n = m->n;
+  a.ng = m->ng;
+  a.sc = sc;
+  a.mt.t = t;
+  a.mt.closed = closed ? 1 : 0;
+  a.mt.n_charges = closed ? n_charges : 0;
+  a.mt.carrier = m->carrier;
+  a.cfg = choose_cfg(m->n, t, P, m->num_sms);
+  a.bx_analytic = 4.0e-7f;
+  a.bx_qp_scale = 0.f;  // derived from the device model's condition number
+  a.recs = (qa::PixRec*)(ws + off_recs);
+  a.flag_list = (int*)(ws + off_list);
+  a.cnt = m->d_cnt;
+  a.out_n = out_n;
+  a.out_U = out_U;
+  a.out_flags = out_flags;
+  a.num_sms = m->num_sms;
+  m->last_cfg = a.cfg;
+  m->last_P = P;
+  e = qa::launch_ground_state(a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ground-state launch");
+  return QA_OK;
+}
+
+int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
+             int n_charges, float* out_mean, float* out_logZ,
+             const float* grad_mean, double* dCdd, double* dCgd, void* stream) {
+  const bool bwd = grad_mean != nullptr;
+  if (!m) return fail(QA_ERR_INVALID, "null model");
+  if (!r) return fail(QA_ERR_INVALID, "null raster");
+  if (!(kT > 0.0) || !std::isfinite(kT)) return fail(QA_ERR_RANGE, "kT=%g must be > 0", kT);
+  if (!(t >= 0.0 && t <= 1.0)) return fail(QA_ERR_RANGE, "threshold %g outside [0, 1]", t);
+  if (closed && (n_charges < 0 || n_charges > 100000))
+    return fail(QA_ERR_RANGE, "n_charges=%d out of range", n_charges);
+  if (!bwd && !out_mean) return fail(QA_ERR_INVALID, "null out_mean");
+  if (bwd && (!dCdd || !dCgd)) return fail(QA_ERR_INVALID, "null gradient output");
+  ScanIn in;
+  in.r = r;
+  qa::Scan sc;
+  int rc = make_scan(m, in, &sc);
+  if (rc) return rc;
+  if ((rc = select_device(m))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long P = sc.P;
+  qa::SearchCfg cfg;
+  if (m->n <= 4) cfg = {4, 0, 4};
+  else if (m->n <= 8) cfg = {5, 4, 8};
+  else cfg = {5, 4, 32};
+  const size_t off_list = align_up(sizeof(qa::Counters), 256);
+  const size_t off_recs = align_up(off_list + sizeof(int) * (size_t)P, 256);
+  const size_t off_part = align_up(off_recs + sizeof(qa::PixRec) * (size_t)P, 256);
+  const size_t total =
+      off_part + (bwd ? sizeof(float) * qa::soft_partials_floats(m->n, P, cfg) : 0);
+  if ((rc = ensure_workspace(m, total))) return rc;
+  char* ws = (char*)m->ws;
+  m->d_cnt = (qa::Counters*)ws;
+  cudaError_t e = cudaMemsetAsync(m->d_cnt, 0, sizeof(qa::Counters), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+
+  qa::GsLaunch g;
+  std::memset(&g, 0, sizeof(g));
+  g.md = m->d_md;
+  g.n = m->n;
+  g.ng = m->ng;
+  g.sc = sc;
+  g.mt.t = t;
+  g.mt.closed = closed ? 1 : 0;
+  g.mt.n_charges = closed ? n_charges : 0;
+  g.mt.carrier = m->carrier;
+  g.cfg = cfg;
+  g.bx_analytic = 4.0e-7f;
+  g.recs = (qa::PixRec*)(ws + off_recs);
+  g.flag_list = (int*)(ws + off_list);
+  g.cnt = m->d_cnt;
+  g.num_sms = m->num_sms;
+  e = qa::launch_prep(g, st);
+  if (e != cudaSuccess) return cuda_fail(e, "prep launch");
+
+  qa::SoftLaunch a;
+  std::memset(&a, 0, sizeof(a));
+  a.md = m->d_md;
+  a.n = m->n;
+  a.ng = m->ng;
+  a.sc = sc;
+  a.mt = g.mt;
+  a.cfg = cfg;
+  a.kT = kT;
+  a.recs = g.recs;
+  a.cnt = m->d_cnt;
+  a.out_mean = out_mean;
+  a.out_logZ = out_logZ;
+  a.grad_mean = grad_mean;
+  a.partials = bwd ? (float*)(ws + off_part) : nullptr;
+  a.dL_dCdd = dCdd;
+  a.dL_dCgd = dCgd;
+  a.num_sms = m->num_sms;
+  m->last_cfg = cfg;
+  m->last_P = P;
+  e = bwd ? qa::launch_soft_backward(a, st) : qa::launch_soft_forward(a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "soft launch");
+  return QA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qa_last_error(void) { return g_err.c_str(); }
+
+int qa_model_create(const double* Cdd, const double* Cgd, int n_dot, int n_gate,
+                    int form, double carrier_sign, qa_model** out) {
+  if (!out) return fail(QA_ERR_INVALID, "null out");
+  *out = nullptr;
+  if (!(carrier_sign == 1.0 || carrier_sign == -1.0))
+    return fail(QA_ERR_INVALID, "carrier_sign must be +1 or -1");
+  qa_model* m = new qa_model();
+  int rc = build_model(n_dot, n_gate, form, Cdd, Cgd, &m->host);
+  if (rc) { delete m; return rc; }
+  m->n = n_dot;
+  m->ng = n_gate;
+  m->form = form;
+  m->carrier = carrier_sign;
+  cudaError_t e = cudaGetDevice(&m->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d_md, sizeof(qa::ModelData));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->d_md, &m->host, sizeof(qa::ModelData), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (m->d_md) cudaFree(m->d_md);
+    delete m;
+    return cuda_fail(e, "model upload");
+  }
+  *out = m;
+  return QA_OK;
+}
+
+int qa_model_update(qa_model* m, const double* Cdd, const double* Cgd) {
+  if (!m) return fail(QA_ERR_INVALID, "null model");
+  qa::ModelData md;
+  int rc = build_model(m->n, m->ng, m->form, Cdd, Cgd, &md);
+  if (rc) return rc;
+  if ((rc = select_device(m))) return rc;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->d_md, &md, sizeof(qa::ModelData), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "model update");
+  m->host = md;
+  m->host_stale = false;
+  return QA_OK;
+}
+
+int qa_model_update_dev(qa_model* m, const double* Cdd_dev, const double* Cgd_dev,
+                        void* stream) {
+  if (!m || !Cdd_dev || !Cgd_dev) return fail(QA_ERR_INVALID, "null argument");
+  int rc = select_device(m);
+  if (rc) return rc;
+  cudaError_t e = qa::launch_model_update(m->d_md, m->n, m->ng, Cdd_dev, Cgd_dev,
+                                          (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "model update launch");
+  m->host_stale = true;
+  return QA_OK;
+}
+
+int qa_model_destroy(qa_model* m) {
+  if (!m) return QA_OK;
+  select_device(m);
+  cudaDeviceSynchronize();
+  if (m->ws) cudaFree(m->ws);
+  if (m->d_md) cudaFree(m->d_md);
+  delete m;
+  return QA_OK;
+}
+
+int qa_model_shape(const qa_model* m, int* n_dot, int* n_gate) {
+  if (!m) return fail(QA_ERR_INVALID, "null model");
+  if (n_dot) *n_dot = m->n;
+  if (n_gate) *n_gate = m->ng;
+  return QA_OK;
+}
+
+int qa_model_get(const qa_model* m, double* Cdd, double* M, double* Cgd) {
+  if (!m) return fail(QA_ERR_INVALID, "null model");
+  qa::ModelData md;
+  int rc = select_device(m);
+  if (rc) return rc;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&md, m->d_md, sizeof(md), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "model read");
+  const int n = m->n, ng = m->ng;
+  if (Cdd) std::memcpy(Cdd, md.Cdd, sizeof(double) * n * n);
+  if (M) std::memcpy(M, md.M, sizeof(double) * n * n);
+  if (Cgd) std::memcpy(Cgd, md.Cgd, sizeof(double) * n * ng);
+  if (md.status != 0) return fail(QA_ERR_NOT_PD, "device update: Cdd is not positive definite");
+  return QA_OK;
+}
+
+int qa_ground_state_open(qa_model* m, const qa_raster* r, double threshold,
+                         int8_t* out_n, double* out_U, uint8_t* out_flags,
+                         void* stream) {
+  if (!r) return fail(QA_ERR_INVALID, "null raster");
+  ScanIn in;
+  in.r = r;
+  return run_ground_state(m, in, threshold, 0, 0, out_n, out_U, out_flags, stream);
+}
+
+int qa_ground_state_closed(qa_model* m, const qa_raster* r, double threshold,
+                           int n_charges, int8_t* out_n, double* out_U,
+                           uint8_t* out_flags, void* stream) {
+  if (!r) return fail(QA_ERR_INVALID, "null raster");
+  ScanIn in;
+  in.r = r;
+  return run_ground_state(m, in, threshold, 1, n_charges, out_n, out_U, out_flags,
+                          stream);
+}
+
+int qa_ground_state_points(qa_model* m, const double* V_dev, long long P,
+                           double threshold, int closed, int n_charges,
+                           int8_t* out_n, double* out_U, uint8_t* out_flags,
+                           void* stream) {
+  ScanIn in;
+  in.V = V_dev;
+  in.P = P;
+  return run_ground_state(m, in, threshold, closed ? 1 : 0, n_charges, out_n, out_U,
+                          out_flags, stream);
+}
+
+int qa_soft_occupation(qa_model* m, const qa_raster* r, double kT,
+                       double threshold, int closed, int n_charges,
+                       float* out_mean, float* out_logZ, void* stream) {
+  return run_soft(m, r, kT, threshold, closed, n_charges, out_mean, out_logZ,
+                  nullptr, nullptr, nullptr, stream);
+}
+
+int qa_soft_occupation_backward(qa_model* m, const qa_raster* r, double kT,
+                                double threshold, int closed, int n_charges,
+                                const float* grad_mean, double* dL_dCdd,
+                                double* dL_dCgd, void* stream) {
+  if (!grad_mean) return fail(QA_ERR_INVALID, "null grad_mean");
+  return run_soft(m, r, kT, threshold, closed, n_charges, nullptr, nullptr,
+                  grad_mean, dL_dCdd, dL_dCgd, stream);
+}
+
+int qa_model_stats(qa_model* m, void* stream, qa_stats* out) {
+  if (!m || !out) return fail(QA_ERR_INVALID, "null argument");
+  std::memset(out, 0, sizeof(*out));
+  int rc = select_device(m);
+  if (rc) return rc;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  if (!m->d_cnt) return QA_OK;
+  qa::Counters c;
+  e = cudaMemcpy(&c, m->d_cnt, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "counters read");
+  out->candidates = (long long)c.candidates;
+  out->evaluated = (long long)c.evaluated;
+  out->qp_pixels = (long long)c.qp;
+  out->flagged = (long long)c.flagged;
+  out->near_tie = (long long)c.near_tie;
+  out->boundary = (long long)c.boundary;
+  out->unresolved = (long long)c.unresolved;
+  out->overflow = (long long)c.overflow;
+  out->doubled = (long long)c.doubled;
+  out->shortlist_max = (long long)c.shortlist_max;
+  out->pixels = m->last_P;
+  out->team = m->last_cfg.T;
+  out->inner_bits = m->last_cfg.L1;
+  out->middle_bits = m->last_cfg.L2;
+  return QA_OK;
+}
+
+}  // extern "C"

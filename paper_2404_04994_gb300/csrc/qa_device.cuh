@@ -1,0 +1,194 @@
+// qa_device.cuh -- device-side building blocks of libqarray (sm_103a).
+//
+// Method (arXiv 2404.04994, Sec. III): per pixel, the continuous minimum of
+// U(x) = 1/2 (x - c)^T M (x - c), M = Cdd^-1, subject to x >= 0 (and
+// 1^T x = N_hat for a closed array), then the argmin of U over the floor /
+// floor + 1 neighbours of that minimum, pruned by Eq. "threshold".
+//
+// Precision plan: c, the analytic minimum and the linear coefficients
+// h = M (base - c) are formed in double-float FP32 arithmetic (error-free
+// transformations, Dekker 1971 / Knuth TAOCP Vol. 2 4.2.2); candidate energies
+// are summed in plain FP32 with a per-pixel error bound; pixels whose decisions
+// fall inside the bound are re-evaluated in FP64 by the recheck kernel.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qa {
+
+constexpr int kMaxDot = 16;
+constexpr int kMaxGate = 64;
+constexpr int kLdM = 17;  // padded smem stride of N x N matrices
+
+enum : unsigned {
+  kFlagNearTie = 1u, kFlagBoundary = 2u, kFlagQP = 4u, kFlagQPCap = 8u,
+  kFlagRechecked = 16u, kFlagDoubled = 32u, kFlagUnresolved = 64u,
+  kFlagOverflow = 128u
+};
+
+// ---------------------------------------------------------------------------
+// double-float arithmetic (value = hi + lo, |lo| <= ulp(hi) / 2)
+// ---------------------------------------------------------------------------
+struct df { float hi, lo; };
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  float e = __fmaf_rn(a, b, -p);
+  return {p, e};
+}
+__device__ __forceinline__ df df_add(df x, df y) {
+  df s = two_sum(x.hi, y.hi);
+  float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return fast_two_sum(s.hi, e);
+}
+__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ df df_sub(df x, df y) { return df_add(x, df_neg(y)); }
+__device__ __forceinline__ df df_mul(df x, df y) {
+  df p = two_prod(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo));
+  return fast_two_sum(p.hi, e);
+}
+__device__ __forceinline__ df df_mul_f(df x, float b) {
+  df p = two_prod(x.hi, b);
+  float e = __fmaf_rn(x.lo, b, p.lo);
+  return fast_two_sum(p.hi, e);
+}
+__device__ __forceinline__ df df_from_double(double v) {
+  float hi = __double2float_rn(v);
+  float lo = __double2float_rn(v - (double)hi);
+  return {hi, lo};
+}
+__device__ __forceinline__ double df_to_double(df x) {
+  return (double)x.hi + (double)x.lo;
+}
+
+// ---------------------------------------------------------------------------
+// shared per-pixel record written by the prep kernel, read by the search
+// ---------------------------------------------------------------------------
+struct __align__(16) PixRec {
+  float h[kMaxDot];     // FP32 of h = M (base - c), formed in double-float
+  float chi[kMaxDot];   // c = s Cgd V as double-float
+  float clo[kMaxDot];
+  short base[kMaxDot];  // floor / rounded charges before the ambiguous +1s
+  unsigned short mask;  // ambiguous dots (both floor and floor + 1 kept)
+  unsigned char k;      // popcount(mask)
+  signed char w;        // closed: number of ambiguous dots taking +1; open: -1
+  unsigned char flags;  // QA flag bits from the prep stage
+  unsigned char pad0[3];
+  float bound;          // FP32 gap below which the pixel is a near-tie
+};
+
+// Device copy of a model (written by the host or by the Cholesky kernel).
+struct ModelData {
+  double Cdd[kMaxDot * kMaxDot];
+  double M[kMaxDot * kMaxDot];        // Cdd^-1
+  double Cgd[kMaxDot * kMaxGate];
+  double vs[kMaxDot];                 // Cdd 1 / (1^T Cdd 1)   (Appendix D)
+  double cond;                        // ||Cdd||_1 ||M||_1
+  int status;                         // 0 ok; nonzero: Cdd not PD on update
+  int pad;
+};
+
+// Where the voltages come from: a raster (by value) or a device list.
+struct Scan {
+  int kind;          // 0 raster, 1 points
+  int W, H;
+  long long P;
+  double x0, dx, y0, dy;
+  double V0[kMaxGate], u[kMaxGate], w[kMaxGate];
+  const double* V;   // points: [P, n_gate]
+};
+
+struct Method {
+  double t;          // threshold
+  int closed;
+  int n_charges;
+  double carrier;    // +1 / -1
+};
+
+struct Counters {
+  unsigned long long candidates, evaluated, qp, flagged, near_tie, boundary,
+      unresolved, overflow, doubled, shortlist_max;
+  unsigned int n_flag;  // length of the recheck list
+  unsigned int pad;
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int ctz_c(unsigned v) {
+  return (v & 1u) ? 0 : 1 + ctz_c(v >> 1);
+}
+__host__ __device__ constexpr unsigned gray_c(unsigned s) { return s ^ (s >> 1); }
+__host__ __device__ constexpr int popc_c(unsigned v) {
+  return v ? (int)(v & 1u) + popc_c(v >> 1) : 0;
+}
+
+// 3-input minimum (PTX ISA 8.8+, sm_100+).
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+  float d;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+  return __fadd2_rn(a, b);
+}
+
+// ---------------------------------------------------------------------------
+// stage (a1): the induced charge c(p) = s Cgd V(p) in double-float
+// ---------------------------------------------------------------------------
+// Block-level setup for a raster: c(ix, iy) = c0 + ix du + iy dw with
+// c0 = s Cgd (V0 + x0 u + y0 w), du = s Cgd u dx, dw = s Cgd w dy (FP64, split).
+struct RasterC {
+  df c0[kMaxDot], du[kMaxDot], dw[kMaxDot];
+};
+
+__device__ inline void raster_setup(const ModelData* md, int n, int ng,
+                                    const Scan& sc, double carrier,
+                                    df* c0, df* du, df* dw) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int g = 0; g < ng; ++g) {
+      double G = md->Cgd[i * ng + g];
+      a += G * (sc.V0[g] + sc.x0 * sc.u[g] + sc.y0 * sc.w[g]);
+      b += G * sc.u[g];
+      c += G * sc.w[g];
+    }
+    c0[i] = df_from_double(carrier * a);
+    du[i] = df_from_double(carrier * b * sc.dx);
+    dw[i] = df_from_double(carrier * c * sc.dy);
+  }
+}
+
+__device__ __forceinline__ df raster_c(df c0, df du, df dw, int ix, int iy) {
+  df a = df_mul_f(du, (float)ix);   // ix, iy < 2^24: exact as floats
+  df b = df_mul_f(dw, (float)iy);
+  return df_add(c0, df_add(a, b));
+}
+
+// c for a point list: s * sum_g Cgd_ig V_g in double-float
+__device__ inline df point_c(const double* Cgd_row, const double* Vp, int ng,
+                             double carrier) {
+  df acc = {0.f, 0.f};
+  for (int g = 0; g < ng; ++g) {
+    df G = df_from_double(carrier * Cgd_row[g]);
+    df v = df_from_double(Vp[g]);
+    acc = df_add(acc, df_mul(G, v));
+  }
+  return acc;
+}
+
+}  // namespace qa

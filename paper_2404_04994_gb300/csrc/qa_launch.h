@@ -1,0 +1,70 @@
+// qa_launch.h -- internal interface between the host ABI (qa_api.cu) and the
+// kernel translation units.  Not part of the public header.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qa_device.cuh"
+
+namespace qa {
+
+// Split of the candidate hypercube used by the search kernel.
+struct SearchCfg {
+  int L1;  // unrolled inner slots (register table of 2^L1 pair terms)
+  int L2;  // unrolled middle slots (compile-time Gray walk)
+  int T;   // lanes per pixel (1..32)
+};
+
+struct GsLaunch {
+  const ModelData* md;
+  int n, ng;
+  Scan sc;
+  Method mt;
+  SearchCfg cfg;
+  float bx_analytic;   // decision margin for double-float continuous minima
+  float bx_qp_scale;   // ... times (1 + max|c| + N_hat) for FP32 QP minima
+  PixRec* recs;        // scratch [P]
+  int* flag_list;      // scratch [P]
+  Counters* cnt;       // scratch, zeroed by the caller
+  int8_t* out_n;
+  double* out_U;
+  uint8_t* out_flags;
+  int num_sms;
+};
+
+// prep -> search -> FP64 recheck, enqueued on `st`.
+cudaError_t launch_ground_state(const GsLaunch& a, cudaStream_t st);
+// prep alone (continuous minimum + candidate set records), for the soft path.
+cudaError_t launch_prep(const GsLaunch& a, cudaStream_t st);
+bool search_cfg_supported(const SearchCfg& c);
+
+struct SoftLaunch {
+  const ModelData* md;
+  int n, ng;
+  Scan sc;
+  Method mt;
+  SearchCfg cfg;
+  float bx_analytic, bx_qp_scale;
+  double kT;
+  PixRec* recs;
+  Counters* cnt;
+  float* out_mean;      // forward outputs
+  float* out_logZ;
+  const float* grad_mean;  // backward input
+  float* partials;      // backward scratch: [blocks][2 * L] double-float sums
+  double* dL_dCdd;      // backward outputs
+  double* dL_dCgd;
+  int num_sms;
+};
+
+cudaError_t launch_soft_forward(const SoftLaunch& a, cudaStream_t st);
+cudaError_t launch_soft_backward(const SoftLaunch& a, cudaStream_t st);
+size_t soft_partials_floats(int n, long long P, const SearchCfg& cfg);
+
+// FP64 Cholesky inverse of a device Cdd into the model (update_dev).
+cudaError_t launch_model_update(ModelData* md, int n, int ng,
+                                const double* Cdd_dev, const double* Cgd_dev,
+                                cudaStream_t st);
+
+}  // namespace qa

@@ -1,0 +1,319 @@
+// qa_search.cuh -- the hot loop: argmin of the candidate energies of one
+// pixel over (a share of) its floor / floor + 1 hypercube (Sec. III.B).
+//
+// Relative to the base configuration, a candidate with ambiguous-slot bits b
+// has energy
+//     E(b) = sum_{j in b} (h_j + M_jj / 2) + sum_{j < l in b} M_jl,
+// h = M (base - c).  The paper evaluates every candidate (2^k of them, Table
+// I).  Instead of an O(k) Gray-code update per candidate, the k slots are
+// split three ways:
+//   inner  (L1 slots): for a fixed rest-state S the 2^L1 energies are
+//          A(S) + sum_{j in b} q_j(S) + P[b], with P[b] = sum_{j<l in b} M_jl
+//          a per-pixel table in registers -- two FP32 adds per candidate
+//          (packed FP32x2 adds, two candidates per instruction) and half a
+//          3-input minimum;
+//   middle (L2 slots): a fully unrolled reflected Gray walk with compile-time
+//          flip positions; one flip updates A, the L1 inner coefficients and
+//          the L2 middle coefficients (L1 + L2 adds per 2^L1 candidates);
+//   outer  (the rest): split across the lanes of a team and rebuilt from
+//          scratch per outer state (no drift across outer states).
+// Closed arrays keep one minimum per inner popcount and pick the one whose
+// total matches N_hat, so they cost the same as open arrays.
+//
+// Near-tie detection: each lane keeps the best and second-best block minima;
+// the winning block is re-evaluated once, candidate by candidate, to get the
+// argmin and the in-block runner-up.
+#pragma once
+
+#include "qa_device.cuh"
+
+namespace qa {
+
+constexpr float kBig = 1.0e30f;
+constexpr float kInf = __builtin_huge_valf();
+
+// Energies of one inner block, min over all 2^L1 patterns (open).
+template <int L1>
+__device__ __forceinline__ float inner_min_open(float A, const float* q,
+                                                const float* P) {
+  constexpr int NI = 1 << L1;
+  float S[NI];
+  S[0] = A;
+  if (L1 >= 1) S[1] = __fadd_rn(A, q[0]);
+#pragma unroll
+  for (int j = 1; j < L1; ++j) {
+    const float2 qq = make_float2(q[j], q[j]);
+#pragma unroll
+    for (int b = 0; b < (1 << j); b += 2) {
+      float2 r = fadd2(make_float2(S[b], S[b + 1]), qq);
+      S[b + (1 << j)] = r.x;
+      S[b + 1 + (1 << j)] = r.y;
+    }
+  }
+  if (NI == 1) return S[0];
+  if (NI == 2) return fminf(S[0], S[1]);
+  // E = S + P (P[0] = P[1] = 0), then a 3-input min tree in two chains
+  float m0 = fminf(S[0], S[1]);
+  float m1 = kInf;
+#pragma unroll
+  for (int b = 2; b < NI; b += 4) {
+    float2 e = fadd2(make_float2(S[b], S[b + 1]), make_float2(P[b], P[b + 1]));
+    m0 = fmin3(m0, e.x, e.y);
+    if (b + 2 < NI) {
+      float2 f = fadd2(make_float2(S[b + 2], S[b + 3]),
+                       make_float2(P[b + 2], P[b + 3]));
+      m1 = fmin3(m1, f.x, f.y);
+    }
+  }
+  return fminf(m0, m1);
+}
+
+// Closed: minimum over the inner patterns with popcount r (kInf if none).
+template <int L1>
+__device__ __forceinline__ float inner_min_closed(float A, const float* q,
+                                                  const float* P, int r) {
+  constexpr int NI = 1 << L1;
+  float S[NI];
+  S[0] = A;
+  if (L1 >= 1) S[1] = __fadd_rn(A, q[0]);
+#pragma unroll
+  for (int j = 1; j < L1; ++j) {
+    const float2 qq = make_float2(q[j], q[j]);
+#pragma unroll
+    for (int b = 0; b < (1 << j); b += 2) {
+      float2 e = fadd2(make_float2(S[b], S[b + 1]), qq);
+      S[b + (1 << j)] = e.x;
+      S[b + 1 + (1 << j)] = e.y;
+    }
+  }
+  float acc[L1 + 1];
+#pragma unroll
+  for (int i = 0; i <= L1; ++i) acc[i] = kInf;
+#pragma unroll
+  for (int b = 0; b < NI; b += 2) {
+    float2 e = (b == 0) ? make_float2(S[0], S[1])
+                        : fadd2(make_float2(S[b], S[b + 1]),
+                                make_float2(P[b], P[b + 1]));
+    if (NI == 1) { acc[0] = S[0]; break; }
+    acc[popc_c(b)] = fminf(acc[popc_c(b)], e.x);
+    acc[popc_c(b + 1)] = fminf(acc[popc_c(b + 1)], e.y);
+  }
+  float res = kInf;
+#pragma unroll
+  for (int i = 0; i <= L1; ++i) res = (i == r) ? acc[i] : res;
+  return res;
+}
+
+// Per-pixel slot data staged by the team: dot of each slot, h of each slot.
+struct SlotView {
+  const int* dot;
+  const float* h;
+  int k;
+  int w;  // closed weight, -1 open
+};
+
+// Rest-state (outer + middle set S) quantities from scratch:
+//   A = E(S), q_j = h_j + M_jj/2 + sum_{s in S} M_{j s} for inner slots.
+template <int L1>
+__device__ __forceinline__ float state_from_scratch(const float* sM,
+                                                    const SlotView& sv,
+                                                    unsigned S_bits,
+                                                    const int* dI,
+                                                    const float* qb, float* q) {
+#pragma unroll
+  for (int j = 0; j < L1; ++j) q[j] = qb[j];
+  float A = 0.f;
+  for (unsigned bits = S_bits; bits; bits &= bits - 1u) {
+    const int s = __ffs(bits) - 1;
+    const int d = sv.dot[s];
+    const float* Mrow = sM + d * kLdM;
+    float add = sv.h[s] + 0.5f * Mrow[d];
+    for (unsigned prev = S_bits & ((1u << s) - 1u); prev; prev &= prev - 1u)
+      add += Mrow[sv.dot[__ffs(prev) - 1]];
+    A += add;
+#pragma unroll
+    for (int j = 0; j < L1; ++j) q[j] += Mrow[dI[j]];
+  }
+  return A;
+}
+
+// Search of one lane's share.  Lane t of a team of T handles the outer
+// patterns o = t, t + T, ...; results: best energy m1 with its full slot
+// pattern b1, and the second-best energy m2 over the lane's candidates.
+// COLLECT: instead, append every (outer, middle) block whose minimum is
+// <= thr to blist (used by the FP64 recheck to shortlist candidates).
+template <int L1, int L2, bool CLOSED, bool COLLECT>
+__device__ __forceinline__ void search_lane(const float* __restrict__ sM,
+                                            const SlotView sv, int t, int T,
+                                            float thr, unsigned* blist,
+                                            unsigned* bcount, unsigned bcap,
+                                            float& m1, unsigned& b1, float& m2,
+                                            unsigned long long& evaluated) {
+  static_assert(L1 >= 2 && L1 <= 6 && L2 >= 0 && L2 <= 5, "search split");
+  constexpr int NI = 1 << L1;
+  constexpr int NM = 1 << L2;
+  const int k = sv.k;
+
+  int dI[L1 > 0 ? L1 : 1];
+  float qb[L1 > 0 ? L1 : 1];
+#pragma unroll
+  for (int j = 0; j < L1; ++j) {
+    if (j < k) {
+      const int d = sv.dot[j];
+      dI[j] = d;
+      qb[j] = sv.h[j] + 0.5f * sM[d * kLdM + d];
+    } else {
+      dI[j] = 0;
+      qb[j] = kBig;  // dummy slot: any pattern using it never wins
+    }
+  }
+  float P[NI];
+  P[0] = 0.f;
+#pragma unroll
+  for (int j = 0; j < L1; ++j) {
+    float Mj[L1 > 0 ? L1 : 1];
+#pragma unroll
+    for (int l = 0; l < j; ++l)
+      Mj[l] = (j < k) ? sM[dI[j] * kLdM + dI[l]] : 0.f;
+#pragma unroll
+    for (int b = 0; b < (1 << j); ++b) {
+      float r = 0.f;
+#pragma unroll
+      for (int l = 0; l < j; ++l)
+        if ((b >> l) & 1) r += Mj[l];
+      P[b | (1 << j)] = P[b] + r;
+    }
+  }
+
+  const int nmid = min(max(k - L1, 0), L2);
+  int dM[L2 > 0 ? L2 : 1];
+  float gb[L2 > 0 ? L2 : 1];
+  float Mmm[L2 > 0 ? L2 : 1][L2 > 0 ? L2 : 1];
+  float Mim[L1 > 0 ? L1 : 1][L2 > 0 ? L2 : 1];
+#pragma unroll
+  for (int m = 0; m < L2; ++m) {
+    const bool live = m < nmid;
+    const int d = live ? sv.dot[L1 + m] : 0;
+    dM[m] = d;
+    gb[m] = live ? sv.h[L1 + m] + 0.5f * sM[d * kLdM + d] : 0.f;
+  }
+#pragma unroll
+  for (int m = 0; m < L2; ++m)
+#pragma unroll
+    for (int m2 = 0; m2 < L2; ++m2)
+      Mmm[m][m2] = (m != m2 && m < nmid && m2 < nmid) ? sM[dM[m] * kLdM + dM[m2]] : 0.f;
+#pragma unroll
+  for (int j = 0; j < L1; ++j)
+#pragma unroll
+    for (int m = 0; m < L2; ++m)
+      Mim[j][m] = (m < nmid) ? sM[dI[j] * kLdM + dM[m]] : 0.f;
+
+  const int nout = max(k - L1 - L2, 0);
+  const unsigned nouter = 1u << nout;
+  float g1 = kInf, g2 = kInf;
+  unsigned blk = 0u;
+  unsigned long long nblocks = 0;
+
+  for (unsigned o = (unsigned)t; o < nouter; o += (unsigned)T) {
+    float q[L1 > 0 ? L1 : 1];
+    const unsigned obits = o << (L1 + L2);
+    float A = state_from_scratch<L1>(sM, sv, obits, dI, qb, q);
+    float gm[L2 > 0 ? L2 : 1];
+#pragma unroll
+    for (int m = 0; m < L2; ++m) {
+      float e = gb[m];
+      for (unsigned bits = obits; bits; bits &= bits - 1u)
+        e += sM[dM[m] * kLdM + sv.dot[__ffs(bits) - 1]];
+      gm[m] = e;
+    }
+    const int popo = __popc(o);
+#pragma unroll
+    for (int s = 0; s < NM; ++s) {
+      if (s > 0) {
+        if (s >= (1 << nmid)) break;
+        const int mb = ctz_c((unsigned)s);
+        const bool up = (gray_c((unsigned)s) >> mb) & 1u;
+        A = up ? A + gm[mb] : A - gm[mb];
+#pragma unroll
+        for (int m = 0; m < L2; ++m)
+          if (m != mb) gm[m] = up ? gm[m] + Mmm[m][mb] : gm[m] - Mmm[m][mb];
+#pragma unroll
+        for (int j = 0; j < L1; ++j)
+          q[j] = up ? q[j] + Mim[j][mb] : q[j] - Mim[j][mb];
+      }
+      float mbk;
+      if (!CLOSED) {
+        mbk = inner_min_open<L1>(A, q, P);
+      } else {
+        const int r = sv.w - popo - popc_c(gray_c((unsigned)s));
+        mbk = inner_min_closed<L1>(A, q, P, r);
+      }
+      ++nblocks;
+      const unsigned id = (o << L2) | gray_c((unsigned)s);
+      if (COLLECT) {
+        if (mbk <= thr) {
+          const unsigned at = atomicAdd(bcount, 1u);
+          if (at < bcap) blist[at] = id;
+        }
+      } else {
+        g2 = fminf(g2, fmaxf(g1, mbk));
+        const bool better = mbk < g1;
+        g1 = better ? mbk : g1;
+        blk = better ? id : blk;
+      }
+    }
+  }
+  evaluated += nblocks * (unsigned long long)NI;
+  if (COLLECT) return;
+
+  m1 = kInf;
+  b1 = 0u;
+  m2 = g2;
+  if (!(g1 < kInf)) return;
+  // re-evaluate the winning block candidate by candidate
+  const unsigned o = blk >> L2, mp = blk & (unsigned)(NM - 1);
+  const unsigned Sbits = (o << (L1 + L2)) | (mp << L1);
+  float q[L1 > 0 ? L1 : 1];
+  const float A = state_from_scratch<L1>(sM, sv, Sbits, dI, qb, q);
+  const int r = CLOSED ? sv.w - __popc(Sbits) : 0;
+  float best = kInf, second = kInf;
+  unsigned bb = 0u;
+#pragma unroll
+  for (int b = 0; b < NI; ++b) {
+    if (CLOSED && popc_c((unsigned)b) != r) continue;
+    float e = A;
+#pragma unroll
+    for (int j = 0; j < L1; ++j)
+      if ((b >> j) & 1) e += q[j];
+    e += P[b];
+    if (e < best) { second = best; best = e; bb = (unsigned)b; }
+    else if (e < second) { second = e; }
+  }
+  m1 = best;
+  b1 = Sbits | bb;
+  m2 = fminf(g2, second);
+}
+
+// Top-two merge of (m1, b1, m2) triples; FP32 ties go to the pattern whose
+// charge vector is lexicographically smaller (bit-reversed order).
+__device__ __forceinline__ void top2_merge(float& m1, unsigned& b1, float& m2,
+                                           float om1, unsigned ob1, float om2) {
+  const bool take = (om1 < m1) || (om1 == m1 && __brev(ob1) < __brev(b1));
+  const float hi = take ? m1 : om1;
+  m2 = fminf(fminf(m2, om2), hi);
+  if (take) { m1 = om1; b1 = ob1; }
+}
+
+// Per-pixel near-tie bound: the FP32 gap below which the order of the best
+// two candidates is not certain.  Every energy is reached through a chain of
+// at most (2^L2 + 2k + 8) FP32 additions (scratch sum of the rest-state, the
+// middle Gray walk, the inner tree), each partial sum bounded by
+// S = sum |h_j| + sum_j M_jj / 2 + sum_{j<l} |M_jl| over the ambiguous slots,
+// and each rounding adds at most 2^-24 S.  The gap threshold is twice that.
+// (The recheck shortlists by the same margin, and the parity tests check on
+// every comparable pixel that no mismatch escapes it.)
+__device__ __forceinline__ float near_tie_bound(float S, int k, int L2) {
+  return 2.0f * (float)((1 << L2) + 2 * k + 8) * 5.9604645e-8f * S;
+}
+
+}  // namespace qa

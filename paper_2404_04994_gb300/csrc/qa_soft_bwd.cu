@@ -1,0 +1,93 @@
+// qa_soft_bwd.cu -- soft occupation backward pass (instantiations) and the
+// device model update.
+#include "qa_soft.cuh"
+
+namespace qa {
+
+cudaError_t launch_soft_backward(const SoftLaunch& a, cudaStream_t st) {
+  return dispatch_soft<true>(a, st);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 Cholesky inverse of a device Cdd (model update on the GPU).  One block:
+// thread 0 factors, threads j < n solve for column j of the inverse.
+// ---------------------------------------------------------------------------
+__global__ void k_model_update(ModelData* md, int n, int ng, const double* Cdd,
+                               const double* Cgd) {
+  __shared__ double L[kMaxDot * kMaxDot];
+  __shared__ int ok;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    md->Cdd[e] = 0.5 * (Cdd[i * n + j] + Cdd[j * n + i]);
+  }
+  for (int e = tid; e < n * ng; e += blockDim.x) md->Cgd[e] = Cgd[e];
+  __syncthreads();
+  if (tid == 0) {
+    ok = 1;
+    for (int j = 0; j < n && ok; ++j) {
+      double d = md->Cdd[j * n + j];
+      for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+      if (!(d > 0.0)) { ok = 0; break; }
+      const double ljj = sqrt(d);
+      L[j * n + j] = ljj;
+      for (int i = j + 1; i < n; ++i) {
+        double s = md->Cdd[i * n + j];
+        for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+        L[i * n + j] = s / ljj;
+      }
+    }
+    md->status = ok ? 0 : 1;
+  }
+  __syncthreads();
+  if (!ok) return;
+  if (tid < n) {
+    const int col = tid;
+    double z[kMaxDot], y[kMaxDot];
+    for (int i = 0; i < n; ++i) {
+      double s = (i == col) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= L[i * n + k] * z[k];
+      z[i] = s / L[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double s = z[i];
+      for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * y[k];
+      y[i] = s / L[i * n + i];
+    }
+    for (int i = 0; i < n; ++i) md->M[i * n + col] = y[i];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) {
+        const double s = 0.5 * (md->M[i * n + j] + md->M[j * n + i]);
+        md->M[i * n + j] = md->M[j * n + i] = s;
+      }
+    double tot = 0.0, n1c = 0.0, n1m = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double r = 0.0;
+      for (int j = 0; j < n; ++j) r += md->Cdd[i * n + j];
+      md->vs[i] = r;
+      tot += r;
+    }
+    for (int i = 0; i < n; ++i) md->vs[i] /= tot;
+    for (int j = 0; j < n; ++j) {
+      double sc = 0.0, sm = 0.0;
+      for (int i = 0; i < n; ++i) {
+        sc += fabs(md->Cdd[i * n + j]);
+        sm += fabs(md->M[i * n + j]);
+      }
+      n1c = fmax(n1c, sc);
+      n1m = fmax(n1m, sm);
+    }
+    md->cond = n1c * n1m;
+  }
+}
+
+cudaError_t launch_model_update(ModelData* md, int n, int ng, const double* Cdd_dev,
+                                const double* Cgd_dev, cudaStream_t st) {
+  k_model_update<<<1, 32, 0, st>>>(md, n, ng, Cdd_dev, Cgd_dev);
+  return cudaGetLastError();
+}
+
+}  // namespace qa
