@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark of the constant-capacitance-model ground-state hot path on GB300.
+
+Workload: the 16-dot 4x4-grid array, open, default algorithm (t = 1), a
+100 x 100 raster over plungers 5 and 6 (seeded synthetic capacitances; the
+paper benchmarks 16-dot 100 x 100 diagrams, Sec. VII).  One step = one whole
+diagram through the C ABI: prep (continuous minimum + candidate set), the
+candidate search, the FP64 recheck of flagged pixels, int8 charges + FP64
+energies + flags written to HBM.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank computes its own
+diagrams (independent shards, no data-path collective; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CSD pixels/s (16-dot 100x100)"
+UNIT = "pixels/s"
+WORKLOAD = "grid16_4x4_open_t1_100x100"
+PAPER_CONTEXT = ("paper: 16-dot 100x100 diagram in < 1 s (> 1e4 px/s) with the JAX "
+                 "default core on a GTX 1080 Ti (Sec. VII) -- other hardware, context only")
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0, period_ms=100):
+        self.path = tempfile.mktemp(prefix="qa_clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+        self.period = period_ms
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", str(self.period)],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+def workload(rank=0):
+    from paper_2404_04994_gb300 import inputs
+    cfg = inputs.grid16(W=100, H=100, t=1.0)
+    return cfg
+
+
+def oracle_rate(cfg, budget_s, rows=None):
+    """FP64 oracle pixels/s on all host cores over a bounded sample of rows."""
+    import oracle
+    W = cfg["raster"]["W"]
+    cores = os.cpu_count() or 1
+    # calibrate on one block of pixels, then size the sample to the budget
+    t0 = time.perf_counter()
+    oracle.ground_state(cfg["Cdd"], cfg["Cgd"], raster=cfg["raster"], t=cfg["t"],
+                        pixels=(0, cores), n_threads=cores)
+    per_px = (time.perf_counter() - t0) / cores
+    if rows is None:
+        npx = max(cores, min(W * cfg["raster"]["H"], int(budget_s / max(per_px, 1e-9))))
+    else:
+        npx = rows * W
+    p0 = (cfg["raster"]["H"] // 2) * W
+    p1 = min(p0 + npx, W * cfg["raster"]["H"])
+    t0 = time.perf_counter()
+    oracle.ground_state(cfg["Cdd"], cfg["Cgd"], raster=cfg["raster"], t=cfg["t"],
+                        pixels=(p0, p1), n_threads=cores)
+    dt = time.perf_counter() - t0
+    return (p1 - p0) / dt, cores, p1 - p0, dt
+
+
+def run_reference(args):
+    from paper_2404_04994_gb300 import dist
+    rank, local, world = dist.env_rank()
+    if rank != 0:
+        return
+    cfg = workload()
+    cores = os.cpu_count() or 1
+    budget = 120.0 / max(1, args.steps + args.warmup)   # whole run ~2 minutes
+    for _ in range(args.warmup):
+        oracle_rate(cfg, budget)
+    rates, total_px, total_t = [], 0, 0.0
+    for _ in range(args.steps):
+        r, cores, npx, dt = oracle_rate(cfg, budget)
+        rates.append(r)
+        total_px += npx
+        total_t += dt
+    value = total_px / total_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_dot": 16, "pixels": 10000,
+                       "threshold": 1.0, "sample": "contiguous pixel rows from the "
+                       "middle of the raster, sized per step to the time budget"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{total_px} pixels over {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2404_04994_gb300 import api, dist
+
+    rank, local, world = dist.init()
+    torch.cuda.set_device(local)
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    cfg = workload(rank)
+    P = cfg["raster"]["W"] * cfg["raster"]["H"]
+    n_dot = cfg["Cdd"].shape[0]
+    m = api.Model(cfg["Cdd"], cfg["Cgd"])
+    h = m.handle
+    ras = cfg["raster"]
+    dev = torch.device("cuda", local)
+    out_n = torch.empty((P, n_dot), dtype=torch.int8, device=dev)
+    out_U = torch.empty(P, dtype=torch.float64, device=dev)
+    out_f = torch.empty(P, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        api.qa_ground_state_open(h, ras, 1.0, out_n, out_U, out_f, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    st0 = m.stats()
+
+    # ---- timed region: K diagrams, L2 flushed between them ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(gpu_index=local).start()
+    time.sleep(0.25)
+    dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    dev_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    dev_ms = dist.max_over_ranks(dev_ms)
+    ms_per_step = dev_ms / args.steps
+    value = world * P / (ms_per_step * 1e-3)
+
+    # ---- roofline: the search kernel timed alone by the library's events ----
+    api.qa_model_set_timing(h, True)
+    search_ms, prep_ms, recheck_ms = [], [], []
+    for _ in range(20):
+        flush.zero_()
+        step()
+        s = m.stats()
+        search_ms.append(s["ms_search"])
+        prep_ms.append(s["ms_prep"])
+        recheck_ms.append(s["ms_recheck"])
+    api.qa_model_set_timing(h, False)
+    st = m.stats()
+    L1, L2 = st["inner_bits"], st["middle_bits"]
+    # FP32 lane-operations per evaluated inner slot: tree add + pair-term add +
+    # one comparison, plus the middle Gray step (L1 + L2 adds and a 3-op top-two
+    # update) shared by the 2^L1 slots of a block
+    ops_per_slot = 3.0 + (L1 + L2 + 3.0) / (1 << L1)
+    ops = st["evaluated"] * ops_per_slot
+    ms_s = statistics.mean(search_ms)
+    achieved = ops / (ms_s * 1e-3) / 1e12
+    sm_max = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = n_sm * 128 * sm_max * 1e6 / 1e12   # FP32 lanes x clock
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
+                "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "k_search<5,4,open>", "ops_per_launch": ops,
+                "ops_per_evaluated_slot": ops_per_slot,
+                "search_ms": round(ms_s, 5), "prep_ms": round(statistics.mean(prep_ms), 5),
+                "recheck_ms": round(statistics.mean(recheck_ms), 5),
+                "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (of nominal "
+                              "unit counts and max clock; MEASURED_PEAKS.json has no FP32 figure)"}
+
+    # ---- end to end: host matrices in, host charge map out ----
+    Cdd, Cgd = cfg["Cdd"], cfg["Cgd"]
+    hn = torch.empty((P, n_dot), dtype=torch.int8, pin_memory=True)
+    hU = torch.empty(P, dtype=torch.float64, pin_memory=True)
+    hf = torch.empty(P, dtype=torch.uint8, pin_memory=True)
+    ke = max(3, min(args.steps, 200))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        api.qa_model_update(h, Cdd, Cgd)
+        step()
+        hn.copy_(out_n, non_blocking=True)
+        hU.copy_(out_U, non_blocking=True)
+        hf.copy_(out_f, non_blocking=True)
+        stream.synchronize()
+    e2e_s = dist.max_over_ranks((time.perf_counter() - t0) / ke)
+    bi = Cdd.nbytes + Cgd.nbytes + 3 * 8 * Cgd.shape[1] + 4 * 8 + 2 * 4
+    bo = hn.numel() + hU.numel() * 8 + hf.numel()
+
+    extra = {"paper_context": PAPER_CONTEXT,
+             "flagged_per_diagram": st["flagged"], "near_tie": st["near_tie"],
+             "boundary": st["boundary"], "qp_pixels": st["qp_pixels"],
+             "unresolved": st["unresolved"], "team": st["team"],
+             "split": [L1, L2], "candidates_per_diagram": st["candidates"],
+             "evaluated_slots_per_diagram": st["evaluated"],
+             "gray_equivalent_gflop_per_diagram": st["candidates"] * (2 * 16 + 4) / 1e9}
+    if not args.no_extra and world == 1:
+        extra.update(extra_measurements(api, torch, flush, args))
+
+    cpu = None
+    if rank == 0 and world == 1:
+        r, cores, npx, dt = oracle_rate(cfg, budget_s=20.0)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{npx} contiguous pixels of the same diagram, FP64 oracle on "
+                         f"{cores} host threads, {dt:.1f} s wall"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_dot": 16, "pixels": P, "threshold": 1.0,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "256 MiB buffer written between steps (outside the "
+                             "per-step events)"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": world * P / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)},
+            "gpu_launches": 3 * args.steps, "clocks": clk, "extra": extra}
+    if rank == 0:
+        print(json.dumps(line))
+    m.close()
+    dist.finalize()
+
+
+def extra_measurements(api, torch, flush, args):
+    """Secondary numbers (not the headline): thresholded search, smaller
+    arrays, the soft occupation and one gradient step."""
+    from paper_2404_04994_gb300 import inputs
+    out = {}
+
+    def timed(fn, reps=30):
+        for _ in range(3):
+            fn()
+        ev = []
+        for _ in range(reps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+    cfg = inputs.grid16(t=0.5)
+    m = api.Model(cfg["Cdd"], cfg["Cgd"])
+    ms = timed(lambda: m.ground_state_open(cfg["raster"], threshold=0.5))
+    out["grid16_t0.5_pixels_per_s"] = 1e4 / (ms * 1e-3)
+    m.close()
+    for name, c, closed in (("double_dot_100x100", inputs.double_dot(), False),
+                            ("chain4_open_200x200", inputs.chain4(), False),
+                            ("chain4_closed_200x200", inputs.chain4(closed=True), True)):
+        m = api.Model(c["Cdd"], c["Cgd"])
+        P = c["raster"]["W"] * c["raster"]["H"]
+        if closed:
+            ms = timed(lambda: m.ground_state_closed(c["raster"], 4))
+        else:
+            ms = timed(lambda: m.ground_state_open(c["raster"]))
+        out[f"{name}_pixels_per_s"] = P / (ms * 1e-3)
+        m.close()
+    try:
+        from paper_2404_04994_gb300 import autograd as qag
+        for kT in (0.01, 0.05):
+            c = inputs.grid8(kT=kT)
+            ms_step = qag.time_grad_step(c, kT, flush=flush)
+            out[f"grad_step_ms_grid8_kT{kT:g}"] = ms_step
+    except ImportError:
+        pass
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extra", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -111,6 +111,11 @@ typedef struct {
     int team;                  /* lanes per pixel used by the search kernel   */
     int inner_bits;            /* unrolled inner / middle bits of the search  */
     int middle_bits;
+    int timed;                 /* 1 when the ms_* fields below are valid      */
+    double ms_prep;            /* device time of each kernel of the last call */
+    double ms_search;          /* (qa_model_set_timing)                       */
+    double ms_recheck;
+    double ms_soft;
 } qa_stats;
 
 /* Create a model from HOST matrices Cdd [n_dot x n_dot] and Cgd
@@ -199,6 +204,12 @@ int qa_soft_occupation_backward(qa_model* m, const qa_raster* r, double kT,
                                 double threshold, int closed, int n_charges,
                                 const float* grad_mean, double* dL_dCdd,
                                 double* dL_dCgd, void* stream);
+
+/* Record CUDA events around each kernel that later calls on this model
+ * enqueue (enable = 1) or stop doing so (0, the default).  The device time of
+ * each kernel of the last call is then reported by qa_model_stats.  Events
+ * are recorded on the call's stream; they add no synchronisation. */
+int qa_model_set_timing(qa_model* m, int enable);
 
 /* Counters of the last call on this model; synchronises `stream` first. */
 int qa_model_stats(qa_model* m, void* stream, qa_stats* out);

@@ -58,7 +58,9 @@ class qa_stats(ctypes.Structure):
         "pixels", "candidates", "evaluated", "qp_pixels", "flagged", "near_tie",
         "boundary", "unresolved", "overflow", "doubled", "shortlist_max")] + [
         ("team", ctypes.c_int), ("inner_bits", ctypes.c_int),
-        ("middle_bits", ctypes.c_int)]
+        ("middle_bits", ctypes.c_int), ("timed", ctypes.c_int),
+        ("ms_prep", ctypes.c_double), ("ms_search", ctypes.c_double),
+        ("ms_recheck", ctypes.c_double), ("ms_soft", ctypes.c_double)]
 
 
 _lib = None
@@ -98,6 +100,7 @@ def load():
                                             ctypes.c_double, ctypes.c_double, I, I,
                                             P, P, P, P]),
         "qa_model_stats": (I, [P, P, ctypes.POINTER(qa_stats)]),
+        "qa_model_set_timing": (I, [P, I]),
         "qa_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -278,6 +281,10 @@ def qa_soft_occupation_backward(m, raster, kT, threshold, closed, n_charges,
         _dev(grad_mean, torch.float32, P * n, "grad_mean"),
         _dev(dL_dCdd, torch.float64, n * n, "dL_dCdd"),
         _dev(dL_dCgd, torch.float64, n * ng, "dL_dCgd"), _stream(stream)))
+
+
+def qa_model_set_timing(m, enable=True):
+    _check(load().qa_model_set_timing(m, int(bool(enable))))
 
 
 def qa_model_stats(m, stream=None):

@@ -98,6 +98,9 @@ struct qa_model {
   qa::Counters* d_cnt = nullptr;
   qa::SearchCfg last_cfg{0, 0, 0};
   long long last_P = 0;
+  bool timing = false;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int last_kind = 0;  // 1 ground state, 2 soft
 };
 
 namespace {
@@ -205,6 +208,12 @@ qa::SearchCfg choose_cfg(int n, double t, long long P, int num_sms) {
   return c;
 }
 
+int prep_team(int n) {
+  int t = 1;
+  while (t < n) t <<= 1;
+  return t;
+}
+
 struct ScanIn {
   const qa_raster* r = nullptr;
   const double* V = nullptr;
@@ -281,6 +290,7 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
   a.mt.n_charges = closed ? n_charges : 0;
   a.mt.carrier = m->carrier;
   a.cfg = choose_cfg(m->n, t, P, m->num_sms);
+  a.prep_team = prep_team(m->n);
   a.bx_analytic = 4.0e-7f;
   a.bx_qp_scale = 0.f;  // derived from the device model's condition number
   a.recs = (qa::PixRec*)(ws + off_recs);
@@ -292,6 +302,8 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
   a.num_sms = m->num_sms;
   m->last_cfg = a.cfg;
   m->last_P = P;
+  a.ev = m->timing ? m->ev : nullptr;
+  m->last_kind = 1;
   e = qa::launch_ground_state(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "ground-state launch");
   return QA_OK;
@@ -343,11 +355,13 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
   g.mt.n_charges = closed ? n_charges : 0;
   g.mt.carrier = m->carrier;
   g.cfg = cfg;
+  g.prep_team = prep_team(m->n);
   g.bx_analytic = 4.0e-7f;
   g.recs = (qa::PixRec*)(ws + off_recs);
   g.flag_list = (int*)(ws + off_list);
   g.cnt = m->d_cnt;
   g.num_sms = m->num_sms;
+  if (m->timing) cudaEventRecord(m->ev[0], st);
   e = qa::launch_prep(g, st);
   if (e != cudaSuccess) return cuda_fail(e, "prep launch");
 
@@ -371,6 +385,8 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
   a.num_sms = m->num_sms;
   m->last_cfg = cfg;
   m->last_P = P;
+  a.ev = m->timing ? m->ev + 4 : nullptr;
+  m->last_kind = 2;
   e = bwd ? qa::launch_soft_backward(a, st) : qa::launch_soft_forward(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "soft launch");
   return QA_OK;
@@ -443,7 +459,23 @@ int qa_model_destroy(qa_model* m) {
   cudaDeviceSynchronize();
   if (m->ws) cudaFree(m->ws);
   if (m->d_md) cudaFree(m->d_md);
+  for (cudaEvent_t& e : m->ev)
+    if (e) cudaEventDestroy(e);
   delete m;
+  return QA_OK;
+}
+
+int qa_model_set_timing(qa_model* m, int enable) {
+  if (!m) return fail(QA_ERR_INVALID, "null model");
+  int rc = select_device(m);
+  if (rc) return rc;
+  if (enable && !m->ev[0]) {
+    for (cudaEvent_t& e : m->ev) {
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return cuda_fail(err, "cudaEventCreate");
+    }
+  }
+  m->timing = enable != 0;
   return QA_OK;
 }
 
@@ -538,6 +570,24 @@ int qa_model_stats(qa_model* m, void* stream, qa_stats* out) {
   out->doubled = (long long)c.doubled;
   out->shortlist_max = (long long)c.shortlist_max;
   out->pixels = m->last_P;
+  if (m->timing && m->last_kind != 0) {
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+    if (m->last_kind == 1 &&
+        cudaEventElapsedTime(&t0, m->ev[0], m->ev[1]) == cudaSuccess &&
+        cudaEventElapsedTime(&t1, m->ev[1], m->ev[2]) == cudaSuccess &&
+        cudaEventElapsedTime(&t2, m->ev[2], m->ev[3]) == cudaSuccess) {
+      out->timed = 1;
+      out->ms_prep = t0;
+      out->ms_search = t1;
+      out->ms_recheck = t2;
+    } else if (m->last_kind == 2 &&
+               cudaEventElapsedTime(&t0, m->ev[0], m->ev[4]) == cudaSuccess &&
+               cudaEventElapsedTime(&t1, m->ev[4], m->ev[5]) == cudaSuccess) {
+      out->timed = 1;
+      out->ms_prep = t0;
+      out->ms_soft = t1;
+    }
+  }
   out->team = m->last_cfg.T;
   out->inner_bits = m->last_cfg.L1;
   out->middle_bits = m->last_cfg.L2;

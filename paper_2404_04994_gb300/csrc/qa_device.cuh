@@ -128,12 +128,20 @@ struct Counters {
 // ---------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------
+// Bit helpers written as straight-line code so that, inside fully unrolled
+// loops, they fold to constants (a recursive form is not folded and turns
+// register-array indices into local-memory accesses).
 __host__ __device__ constexpr int ctz_c(unsigned v) {
-  return (v & 1u) ? 0 : 1 + ctz_c(v >> 1);
+  return (v & 0x1u) ? 0 : (v & 0x2u) ? 1 : (v & 0x4u) ? 2 : (v & 0x8u) ? 3
+       : (v & 0x10u) ? 4 : (v & 0x20u) ? 5 : (v & 0x40u) ? 6 : (v & 0x80u) ? 7
+       : (v & 0x100u) ? 8 : (v & 0x200u) ? 9 : 10;
 }
 __host__ __device__ constexpr unsigned gray_c(unsigned s) { return s ^ (s >> 1); }
 __host__ __device__ constexpr int popc_c(unsigned v) {
-  return v ? (int)(v & 1u) + popc_c(v >> 1) : 0;
+  return (int)(v & 1u) + (int)((v >> 1) & 1u) + (int)((v >> 2) & 1u) +
+         (int)((v >> 3) & 1u) + (int)((v >> 4) & 1u) + (int)((v >> 5) & 1u) +
+         (int)((v >> 6) & 1u) + (int)((v >> 7) & 1u) + (int)((v >> 8) & 1u) +
+         (int)((v >> 9) & 1u);
 }
 
 // 3-input minimum (PTX ISA 8.8+, sm_100+).

@@ -9,7 +9,8 @@ namespace qa {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPrepThreads = 128;
 constexpr int kSearchThreads = 128;
-constexpr int kRecheckThreads = 256;
+constexpr int kRecheckThreads = 128;
+constexpr int kRecheckL1 = 4, kRecheckL2 = 3;  // 2^9 outer states at k = 16
 constexpr unsigned kBcap = 1024;
 
 // number of k-subsets of size w (k <= 16)
@@ -49,6 +50,10 @@ __device__ inline void stage_model(const ModelData* md, int n, float* sMhi,
 
 // ---------------------------------------------------------------------------
 // (a1)-(a4): induced charge, continuous minimum, candidate set, h = M(base-c)
+//
+// A team of TP lanes (a power of two >= N, at most 16) prepares one pixel,
+// lane i owning dot i; team-wide sums, ballots and gathers use shuffles
+// restricted to the team's lanes, so teams of one warp may diverge.
 // ---------------------------------------------------------------------------
 template <bool CLOSED>
 __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch a) {
@@ -57,123 +62,174 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch a) {
   __shared__ float sv[kMaxDot];
   __shared__ float s_s;
   __shared__ df sc0[kMaxDot], sdu[kMaxDot], sdw[kMaxDot], svs[kMaxDot];
+  __shared__ float sx[kPrepThreads];
+  __shared__ int sst[kPrepThreads];
   const int n = a.n;
   stage_model(a.md, n, sMhi, sMlo, sCdd, sv, &s_s);
   if (a.sc.kind == 0) raster_setup(a.md, n, a.ng, a.sc, a.mt.carrier, sc0, sdu, sdw);
   for (int i = threadIdx.x; i < n; i += blockDim.x) svs[i] = df_from_double(a.md->vs[i]);
   __syncthreads();
-
   // decision margin of an FP32 QP minimum: 8 cond(Cdd) (n + 1) u32 per unit
   // of (1 + max|c| + N_hat)
   const float bx_qp_scale =
       a.bx_qp_scale > 0.f ? a.bx_qp_scale
                           : 8.f * (float)a.md->cond * (float)(n + 1) * 5.9604645e-8f;
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned long long my_cand = 0, my_qp = 0, my_doubled = 0;
-  if (p < a.sc.P) {
-    df c[kMaxDot];
+  const bool model_bad = a.md->status != 0;
+
+  const int TP = a.prep_team;
+  const int lt = threadIdx.x & (TP - 1);
+  const int lane = threadIdx.x & 31;
+  const int tbase = lane & ~(TP - 1);                   // team's first lane
+  const unsigned tmask = (TP == 32 ? 0xffffffffu : ((1u << TP) - 1u)) << tbase;
+  const long long p = (long long)blockIdx.x * (kPrepThreads / TP) + threadIdx.x / TP;
+  const bool active = p < a.sc.P;
+  const bool live = active && lt < n;
+  const int nhat = a.mt.n_charges;
+
+  // team reductions over lanes (dead lanes contribute zero)
+  auto tsum_f = [&](float v) {
+    for (int off = 1; off < TP; off <<= 1) v += __shfl_xor_sync(tmask, v, off, TP);
+    return v;
+  };
+  auto tmax_f = [&](float v) {
+    for (int off = 1; off < TP; off <<= 1) v = fmaxf(v, __shfl_xor_sync(tmask, v, off, TP));
+    return v;
+  };
+  auto tsum_i = [&](int v) {
+    for (int off = 1; off < TP; off <<= 1) v += __shfl_xor_sync(tmask, v, off, TP);
+    return v;
+  };
+  auto tsum_df = [&](df v) {
+    for (int off = 1; off < TP; off <<= 1) {
+      df o;
+      o.hi = __shfl_xor_sync(tmask, v.hi, off, TP);
+      o.lo = __shfl_xor_sync(tmask, v.lo, off, TP);
+      v = df_add(v, o);
+    }
+    return v;
+  };
+  auto tballot = [&](bool pred) { return (__ballot_sync(tmask, pred) & tmask) >> tbase; };
+
+  if (!active) return;  // whole teams retire together
+
+  // (a1) c_i
+  df c = {0.f, 0.f};
+  if (live) {
     if (a.sc.kind == 0) {
       const int ix = (int)(p % a.sc.W), iy = (int)(p / a.sc.W);
-#pragma unroll
-      for (int i = 0; i < kMaxDot; ++i)
-        if (i < n) c[i] = raster_c(sc0[i], sdu[i], sdw[i], ix, iy);
+      c = raster_c(sc0[lt], sdu[lt], sdw[lt], ix, iy);
     } else {
-      for (int i = 0; i < n; ++i)
-        c[i] = point_c(&a.md->Cgd[i * a.ng], &a.sc.V[p * a.ng], a.ng, a.mt.carrier);
+      c = point_c(&a.md->Cgd[lt * a.ng], &a.sc.V[p * a.ng], a.ng, a.mt.carrier);
     }
-    const int nhat = a.mt.n_charges;
-    df x[kMaxDot];
-    if (!CLOSED) {
-#pragma unroll
-      for (int i = 0; i < kMaxDot; ++i)
-        if (i < n) x[i] = c[i];
+  }
+  // (a2) analytic continuous minimum (Appendix C / D)
+  df x = c;
+  if (CLOSED) {
+    const df cs = tsum_df(c);
+    const df lam = df_sub({(float)nhat, 0.f}, cs);  // N_hat <= 2^24
+    if (live) x = df_add(c, df_mul(lam, svs[lt]));
+  }
+  const unsigned A =
+      tballot(live && (x.hi < 0.f || (x.hi == 0.f && x.lo < 0.f)));
+  unsigned flags = 0u;
+  float bx = a.bx_analytic;
+  const float cmax = tmax_f(live ? fabsf(c.hi + c.lo) : 0.f);
+  if (A) {  // (a3) QP, solved by the team's first lane
+    flags |= kFlagQP;
+    if (CLOSED && nhat == 0) {
+      x = {0.f, 0.f};
     } else {
-      df cs = {0.f, 0.f};
-#pragma unroll
-      for (int i = 0; i < kMaxDot; ++i)
-        if (i < n) cs = df_add(cs, c[i]);
-      const df lam = df_sub({(float)nhat, 0.f}, cs);  // N_hat <= 2^24
-#pragma unroll
-      for (int i = 0; i < kMaxDot; ++i)
-        if (i < n) x[i] = df_add(c[i], df_mul(lam, svs[i]));
-    }
-    unsigned A = 0u;
-#pragma unroll
-    for (int i = 0; i < kMaxDot; ++i)
-      if (i < n && (x[i].hi < 0.f || (x[i].hi == 0.f && x[i].lo < 0.f))) A |= 1u << i;
-    unsigned flags = 0u;
-    float bx = a.bx_analytic;
-    if (A) {
-      flags |= kFlagQP;
-      my_qp = 1;
-      if (CLOSED && nhat == 0) {
-#pragma unroll
-        for (int i = 0; i < kMaxDot; ++i) x[i] = {0.f, 0.f};
-      } else {
+      const float scale = 1.f + cmax + (float)nhat;
+      bx = fmaxf(bx, bx_qp_scale * scale);
+      sx[threadIdx.x] = c.hi + c.lo;
+      __syncwarp(tmask);
+      if (lt == 0) {
         float cf[kMaxDot], xf[kMaxDot];
-        float cmax = 0.f;
-        for (int i = 0; i < n; ++i) {
-          cf[i] = c[i].hi + c[i].lo;
-          cmax = fmaxf(cmax, fabsf(cf[i]));
-        }
-        const float scale = 1.f + cmax + (float)nhat;
-        bx = fmaxf(bx, bx_qp_scale * scale);
-        const int st = qp_active_set<float>(n, sCdd, kLdM, cf, CLOSED, (float)nhat,
-                                            sv, s_s, A, 0.25f * bx_qp_scale * scale,
+        for (int j = 0; j < n; ++j) cf[j] = sx[threadIdx.x + j];
+        const int st = qp_active_set<float>(n, sCdd, kLdM, cf, CLOSED, (float)nhat, sv,
+                                            s_s, A, 0.25f * bx_qp_scale * scale,
                                             4 * n + 4, xf);
-        if (st != 0) flags |= kFlagQPCap;
-        for (int i = 0; i < n; ++i) x[i] = {xf[i], 0.f};
+        for (int j = 0; j < n; ++j) sx[threadIdx.x + j] = xf[j];
+        sst[threadIdx.x] = st;
       }
+      __syncwarp(tmask);
+      if (live) x = {sx[threadIdx.x], 0.f};
+      if (sst[threadIdx.x - lt] != 0) flags |= kFlagQPCap;
+      __syncwarp(tmask);
     }
-    int base[kMaxDot];
-    unsigned mask;
-    int w;
-    candidate_set_df(n, x, a.mt.t, CLOSED, nhat, bx, base, mask, w, flags);
-    if (flags & kFlagDoubled) my_doubled = 1;
+  }
 
-    // h = M (base - c) in double-float
-    PixRec rec;
-    df r[kMaxDot];
-#pragma unroll
-    for (int j = 0; j < kMaxDot; ++j)
-      if (j < n) r[j] = df_sub({(float)base[j], 0.f}, c[j]);
-    float S = 0.f;
-    for (int i = 0; i < n; ++i) {
-      df acc = {0.f, 0.f};
-      for (int j = 0; j < n; ++j)
-        acc = df_add(acc, df_mul({sMhi[i * kLdM + j], sMlo[i * kLdM + j]}, r[j]));
-      const float hi = acc.hi + acc.lo;
-      rec.h[i] = hi;
-      if ((mask >> i) & 1u) {
-        S += fabsf(hi) + 0.5f * sMhi[i * kLdM + i];
-        for (unsigned m2 = mask & ((1u << i) - 1u); m2; m2 &= m2 - 1u)
-          S += fabsf(sMhi[i * kLdM + (__ffs(m2) - 1)]);
-      }
+  // (a4) candidate set; the closed doubling loop is team-uniform
+  double tt = a.mt.t;
+  unsigned mask = 0u;
+  int w = -1, base = 0;
+  bool amb = false;
+  for (int iter = 0; iter < 40; ++iter) {
+    const float th = __double2float_rn(0.5 * tt);
+    bool bnd = false;
+    if (live) {
+      df xi = x;
+      if (xi.hi < 0.f || (xi.hi == 0.f && xi.lo < 0.f)) xi = {0.f, 0.f};
+      float fl = floorf(xi.hi);
+      if (xi.hi == fl && xi.lo < 0.f) fl -= 1.f;
+      const float fr = __fadd_rn(__fsub_rn(xi.hi, fl), xi.lo);
+      amb = fabsf(fr - 0.5f) <= th;
+      base = (int)fl + ((!amb && fr >= 0.5f) ? 1 : 0);
+      bnd = (xi.hi >= 0.5f - bx && fminf(fr, 1.f - fr) < bx) ||
+            (tt < 1.0 && fabsf(fabsf(fr - 0.5f) - th) < bx);
     }
-    for (int i = 0; i < kMaxDot; ++i) {
-      const bool live = i < n;
-      rec.chi[i] = live ? c[i].hi : 0.f;
-      rec.clo[i] = live ? c[i].lo : 0.f;
-      rec.base[i] = live ? (short)base[i] : (short)0;
-      if (!live) rec.h[i] = 0.f;
+    if (tballot(bnd)) flags |= kFlagBoundary;
+    mask = tballot(live && amb);
+    const int sum = tsum_i(live ? base : 0);
+    if (!CLOSED) break;
+    w = nhat - sum;
+    if (w >= 0 && w <= __popc(mask)) break;
+    if (tt >= 1.0) {  // impossible in exact arithmetic: settle in FP64
+      flags |= kFlagBoundary;
+      w = w < 0 ? 0 : __popc(mask);
+      break;
     }
-    const int k = __popc(mask);
-    rec.mask = (unsigned short)mask;
-    rec.k = (unsigned char)k;
-    rec.w = (signed char)(CLOSED ? w : -1);
-    rec.flags = (unsigned char)flags;
-    rec.pad0[0] = rec.pad0[1] = rec.pad0[2] = 0;
-    rec.bound = near_tie_bound(S, k, a.cfg.L2);
-    a.recs[p] = rec;
+    tt = (tt <= 0.0) ? 1.0 : fmin(2.0 * tt, 1.0);
+    flags |= kFlagDoubled;
+  }
+  if (model_bad) flags |= kFlagUnresolved;
+
+  // h_i = (M (base - c))_i in double-float, r_j gathered from the team
+  const df r = df_sub({(float)base, 0.f}, c);
+  df acc = {0.f, 0.f};
+  for (int j = 0; j < n; ++j) {
+    df rj;
+    rj.hi = __shfl_sync(tmask, r.hi, j, TP);
+    rj.lo = __shfl_sync(tmask, r.lo, j, TP);
+    if (live) acc = df_add(acc, df_mul({sMhi[lt * kLdM + j], sMlo[lt * kLdM + j]}, rj));
+  }
+  const float h = acc.hi + acc.lo;
+  float Si = 0.f;
+  if (live && amb) {
+    Si = fabsf(h) + 0.5f * sMhi[lt * kLdM + lt];
+    for (unsigned m2 = mask & ((1u << lt) - 1u); m2; m2 &= m2 - 1u)
+      Si += fabsf(sMhi[lt * kLdM + (__ffs(m2) - 1)]);
+  }
+  const float S = tsum_f(Si);
+  const int k = __popc(mask);
+
+  PixRec* rec = a.recs + p;
+  if (live) {
+    rec->h[lt] = h;
+    rec->chi[lt] = c.hi;
+    rec->clo[lt] = c.lo;
+    rec->base[lt] = (short)base;
+  }
+  unsigned long long my_cand = 0, my_qp = 0, my_doubled = 0;
+  if (lt == 0) {
+    rec->mask = (unsigned short)mask;
+    rec->k = (unsigned char)k;
+    rec->w = (signed char)(CLOSED ? w : -1);
+    rec->flags = (unsigned char)flags;
+    rec->bound = near_tie_bound(S, k, a.cfg.L2);
     my_cand = CLOSED ? binom(k, w) : (1ull << k);
-  }
-  // counters: warp sums, one atomic per warp
-  for (int off = 16; off > 0; off >>= 1) {
-    my_cand += __shfl_xor_sync(kFull, my_cand, off);
-    my_qp += __shfl_xor_sync(kFull, my_qp, off);
-    my_doubled += __shfl_xor_sync(kFull, my_doubled, off);
-  }
-  if ((threadIdx.x & 31) == 0) {
+    my_qp = (flags & kFlagQP) ? 1 : 0;
+    my_doubled = (flags & kFlagDoubled) ? 1 : 0;
     if (my_cand) atomicAdd(&a.cnt->candidates, my_cand);
     if (my_qp) atomicAdd(&a.cnt->qp, my_qp);
     if (my_doubled) atomicAdd(&a.cnt->doubled, my_doubled);
@@ -226,31 +282,25 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch a) {
   }
 
   // epilogue: n* = base + bits, U(n*) = 1/2 r^T M r in double-float (team
-  // lanes split the rows)
+  // lanes split the rows; no per-thread arrays, so nothing lands in local
+  // memory)
   df u = {0.f, 0.f};
-  int nst[kMaxDot];
   unsigned flags = 0u;
   if (active) {
-    flags = rec->flags;
-#pragma unroll
-    for (int i = 0; i < kMaxDot; ++i) {
-      int v = 0;
-      if (i < n) {
-        v = rec->base[i];
-        if ((mask >> i) & 1u) v += (int)((b1 >> __popc(mask & ((1u << i) - 1u))) & 1u);
-      }
-      nst[i] = v;
-    }
-    df r[kMaxDot];
-#pragma unroll
-    for (int j = 0; j < kMaxDot; ++j)
-      r[j] = (j < n) ? df_sub({(float)nst[j], 0.f}, {rec->chi[j], rec->clo[j]})
-                     : df{0.f, 0.f};
     for (int i = lt; i < n; i += T) {
       df acc = {0.f, 0.f};
-      for (int j = 0; j < n; ++j)
-        acc = df_add(acc, df_mul({sM[i * kLdM + j], sMlo[i * kLdM + j]}, r[j]));
-      u = df_add(u, df_mul(acc, r[i]));
+      for (int j = 0; j < n; ++j) {
+        int nj = rec->base[j];
+        if ((mask >> j) & 1u) nj += (int)((b1 >> __popc(mask & ((1u << j) - 1u))) & 1u);
+        const df rj = df_sub({(float)nj, 0.f}, {rec->chi[j], rec->clo[j]});
+        acc = df_add(acc, df_mul({sM[i * kLdM + j], sMlo[i * kLdM + j]}, rj));
+      }
+      int ni = rec->base[i];
+      if ((mask >> i) & 1u) ni += (int)((b1 >> __popc(mask & ((1u << i) - 1u))) & 1u);
+      const df ri = df_sub({(float)ni, 0.f}, {rec->chi[i], rec->clo[i]});
+      u = df_add(u, df_mul(acc, ri));
+      if (ni > 127) { ni = 127; flags |= kFlagOverflow; }
+      a.out_n[p * n + i] = (int8_t)ni;
     }
   }
   for (int off = 1; off < T; off <<= 1) {
@@ -258,17 +308,12 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch a) {
     o.hi = __shfl_xor_sync(kFull, u.hi, off);
     o.lo = __shfl_xor_sync(kFull, u.lo, off);
     u = df_add(u, o);
+    flags |= __shfl_xor_sync(kFull, flags, off);
   }
   unsigned long long my_nt = 0, my_bd = 0, my_fl = 0, my_ov = 0;
   if (active) {
+    flags |= rec->flags;
     if (!(m2 - m1 > rec->bound)) flags |= kFlagNearTie;
-    for (int i = lt; i < n; i += T) {
-      int v = nst[i];
-      if (v > 127) { v = 127; flags |= kFlagOverflow; }
-      a.out_n[p * n + i] = (int8_t)v;
-    }
-    for (int i = 0; i < n; ++i)
-      if (nst[i] > 127) flags |= kFlagOverflow;
     if (lt == 0) {
       if (a.out_U) a.out_U[p] = 0.5 * df_to_double(u);
       if (flags & (kFlagNearTie | kFlagBoundary | kFlagQPCap)) {
@@ -303,29 +348,31 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch a) {
 // ---------------------------------------------------------------------------
 // (a7): FP64 recheck of flagged pixels.  One block per pixel (grid-stride
 // over the list written by the search kernel):
-//   1. the continuous minimum and candidate set again, in FP64;
-//   2. the FP32 search over that set with all 256 threads -> m1;
+//   1. c, the continuous minimum and the candidate set again, in FP64
+//      (c and h by N threads in parallel, the minimum by one thread);
+//   2. the FP32 search over that set with all threads -> m1;
 //   3. the same search collecting every block whose minimum is within the
 //      near-tie bound of m1 (the exact argmin is guaranteed to be there);
 //   4. exact FP64 energies of those candidates, ties to the
 //      lexicographically smallest charge vector.
 // ---------------------------------------------------------------------------
-template <int L1, int L2, bool CLOSED>
+template <bool CLOSED>
 __global__ void __launch_bounds__(kRecheckThreads) k_recheck(GsLaunch a) {
+  constexpr int L1 = kRecheckL1, L2 = kRecheckL2;
   constexpr int NI = 1 << L1;
   constexpr int NM = 1 << L2;
+  constexpr int NW = kRecheckThreads / 32;
   __shared__ float sM[kMaxDot * kLdM];
   __shared__ int sdot[kMaxDot];
   __shared__ float sh[kMaxDot];
   __shared__ double sh64[kMaxDot], sc64[kMaxDot];
   __shared__ int sbase[kMaxDot];
   __shared__ int sk, sw, sstatus;
-  __shared__ unsigned sflags;
+  __shared__ unsigned smask, sflags;
   __shared__ float sbound;
-  __shared__ float rm1[kRecheckThreads / 32], rm2[kRecheckThreads / 32];
-  __shared__ unsigned rb1[kRecheckThreads / 32];
-  __shared__ double re[kRecheckThreads / 32];
-  __shared__ unsigned rbits[kRecheckThreads / 32];
+  __shared__ float rm1[NW];
+  __shared__ double re[NW];
+  __shared__ unsigned rbits[NW];
   __shared__ unsigned blist[kBcap];
   __shared__ unsigned bcount;
   const int n = a.n;
@@ -337,34 +384,19 @@ __global__ void __launch_bounds__(kRecheckThreads) k_recheck(GsLaunch a) {
 
   for (unsigned it = blockIdx.x; it < nflag; it += gridDim.x) {
     const long long p = a.flag_list[it];
+    if (tid < n) sc64[tid] = pixel_c_f64(a.md, a.ng, a.sc, a.mt.carrier, p, tid);
+    __syncthreads();
     if (tid == 0) {
       double c[kMaxDot];
       int base[kMaxDot];
       unsigned mask = 0u, fl = 0u;
       int w = -1;
-      const int st = prep_pixel_f64(a.md, n, a.ng, a.sc, a.mt, p, c, base, mask, w, fl);
-      sstatus = st;
+      for (int i = 0; i < n; ++i) c[i] = sc64[i];
+      sstatus = (a.md->status != 0) ? -1 : settle_pixel_f64(a.md, n, a.mt, c, base, mask, w, fl);
       sflags = fl;
-      float S = 0.f;
-      int s = 0;
-      for (int i = 0; i < n; ++i) {
-        sc64[i] = c[i];
-        sbase[i] = base[i];
-      }
-      for (int i = 0; i < n; ++i) {
-        if (!((mask >> i) & 1u)) continue;
-        double h = 0.0;
-        for (int j = 0; j < n; ++j) h += a.md->M[i * n + j] * ((double)base[j] - c[j]);
-        sdot[s] = i;
-        sh64[s] = h;
-        sh[s] = __double2float_rn(h);
-        S += fabsf(sh[s]) + 0.5f * sM[i * kLdM + i];
-        for (int q = 0; q < s; ++q) S += fabsf(sM[i * kLdM + sdot[q]]);
-        ++s;
-      }
-      sk = s;
+      smask = mask;
       sw = CLOSED ? w : -1;
-      sbound = near_tie_bound(S, s, L2);
+      for (int i = 0; i < n; ++i) sbase[i] = base[i];
       bcount = 0u;
     }
     __syncthreads();
@@ -376,22 +408,38 @@ __global__ void __launch_bounds__(kRecheckThreads) k_recheck(GsLaunch a) {
       __syncthreads();
       continue;
     }
+    const unsigned mask = smask;
+    if (tid < n && ((mask >> tid) & 1u)) {
+      double h = 0.0;
+      for (int j = 0; j < n; ++j) h += a.md->M[tid * n + j] * ((double)sbase[j] - sc64[j]);
+      const int s = __popc(mask & ((1u << tid) - 1u));
+      sdot[s] = tid;
+      sh64[s] = h;
+      sh[s] = __double2float_rn(h);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const int k = __popc(mask);
+      float S = 0.f;
+      for (int s = 0; s < k; ++s) {
+        S += fabsf(sh[s]) + 0.5f * sM[sdot[s] * kLdM + sdot[s]];
+        for (int q = 0; q < s; ++q) S += fabsf(sM[sdot[s] * kLdM + sdot[q]]);
+      }
+      sk = k;
+      sbound = near_tie_bound(S, k, L2);
+    }
+    __syncthreads();
     const SlotView sv{sdot, sh, sk, sw};
     float m1, m2;
     unsigned b1;
     unsigned long long ev = 0;
     search_lane<L1, L2, CLOSED, false>(sM, sv, tid, kRecheckThreads, 0.f, nullptr,
                                        nullptr, 0u, m1, b1, m2, ev);
-    for (int off = 16; off > 0; off >>= 1) {
-      const float om1 = __shfl_xor_sync(kFull, m1, off);
-      const unsigned ob1 = __shfl_xor_sync(kFull, b1, off);
-      const float om2 = __shfl_xor_sync(kFull, m2, off);
-      top2_merge(m1, b1, m2, om1, ob1, om2);
-    }
-    if (lane == 0) { rm1[wid] = m1; rm2[wid] = m2; rb1[wid] = b1; }
+    for (int off = 16; off > 0; off >>= 1) m1 = fminf(m1, __shfl_xor_sync(kFull, m1, off));
+    if (lane == 0) rm1[wid] = m1;
     __syncthreads();
     m1 = kInf;
-    for (int i = 0; i < kRecheckThreads / 32; ++i) m1 = fminf(m1, rm1[i]);
+    for (int i = 0; i < NW; ++i) m1 = fminf(m1, rm1[i]);
     const float thr = m1 + sbound;
     float d1, d2;
     unsigned db;
@@ -409,7 +457,7 @@ __global__ void __launch_bounds__(kRecheckThreads) k_recheck(GsLaunch a) {
       const unsigned id = blist[idx / NI];
       const unsigned b = idx % NI;
       const unsigned bits = ((id >> L2) << (L1 + L2)) | ((id & (NM - 1)) << L1) | b;
-      if (k < 32 && (bits >> k) != 0u) continue;
+      if ((bits >> k) != 0u) continue;
       if (CLOSED && __popc(bits) != sw) continue;
       double E = 0.0;
       for (unsigned m = bits; m; m &= m - 1u) {
@@ -432,7 +480,7 @@ __global__ void __launch_bounds__(kRecheckThreads) k_recheck(GsLaunch a) {
     if (lane == 0) { re[wid] = best; rbits[wid] = bbits; }
     __syncthreads();
     if (tid == 0) {
-      for (int i = 1; i < kRecheckThreads / 32; ++i)
+      for (int i = 1; i < NW; ++i)
         if (re[i] < best || (re[i] == best && __brev(rbits[i]) < __brev(bbits))) {
           best = re[i];
           bbits = rbits[i];
@@ -472,17 +520,23 @@ __global__ void __launch_bounds__(kRecheckThreads) k_recheck(GsLaunch a) {
 template <int L1, int L2, bool CLOSED>
 static cudaError_t run(const GsLaunch& a, cudaStream_t st) {
   const long long P = a.sc.P;
-  const unsigned gp = (unsigned)((P + kPrepThreads - 1) / kPrepThreads);
+  const long long tpb = kPrepThreads / a.prep_team;
+  const unsigned gp = (unsigned)((P + tpb - 1) / tpb);
+  if (a.ev) cudaEventRecord(a.ev[0], st);
   k_prep<CLOSED><<<gp, kPrepThreads, 0, st>>>(a);
+  if (a.ev) cudaEventRecord(a.ev[1], st);
   const int teams = kSearchThreads / a.cfg.T;
   const unsigned gs = (unsigned)((P + teams - 1) / teams);
   k_search<L1, L2, CLOSED><<<gs, kSearchThreads, 0, st>>>(a);
-  k_recheck<5, 4, CLOSED><<<2 * a.num_sms, kRecheckThreads, 0, st>>>(a);
+  if (a.ev) cudaEventRecord(a.ev[2], st);
+  k_recheck<CLOSED><<<2 * a.num_sms, kRecheckThreads, 0, st>>>(a);
+  if (a.ev) cudaEventRecord(a.ev[3], st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_prep(const GsLaunch& a, cudaStream_t st) {
-  const unsigned gp = (unsigned)((a.sc.P + kPrepThreads - 1) / kPrepThreads);
+  const long long tpb = kPrepThreads / a.prep_team;
+  const unsigned gp = (unsigned)((a.sc.P + tpb - 1) / tpb);
   if (gp == 0) return cudaSuccess;
   if (a.mt.closed)
     k_prep<true><<<gp, kPrepThreads, 0, st>>>(a);

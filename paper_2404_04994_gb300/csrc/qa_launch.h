@@ -22,6 +22,7 @@ struct GsLaunch {
   Scan sc;
   Method mt;
   SearchCfg cfg;
+  int prep_team;       // lanes per pixel in the prep kernel (pow2 >= n, <= 16)
   float bx_analytic;   // decision margin for double-float continuous minima
   float bx_qp_scale;   // ... times (1 + max|c| + N_hat) for FP32 QP minima
   PixRec* recs;        // scratch [P]
@@ -31,6 +32,7 @@ struct GsLaunch {
   double* out_U;
   uint8_t* out_flags;
   int num_sms;
+  cudaEvent_t* ev;     // optional: 4 events recorded around prep/search/recheck
 };
 
 // prep -> search -> FP64 recheck, enqueued on `st`.
@@ -56,6 +58,7 @@ struct SoftLaunch {
   double* dL_dCdd;      // backward outputs
   double* dL_dCgd;
   int num_sms;
+  cudaEvent_t* ev;     // optional: events around the soft kernel(s)
 };
 
 cudaError_t launch_soft_forward(const SoftLaunch& a, cudaStream_t st);

@@ -173,26 +173,31 @@ __device__ __forceinline__ int candidate_set_f64(int n, const double* x,
 }
 
 // ---------------------------------------------------------------------------
-// FP64 preparation of one pixel (recheck path; one thread).
+// FP64 preparation of one pixel (recheck path).
 // ---------------------------------------------------------------------------
-__device__ inline int prep_pixel_f64(const ModelData* md, int n, int ng,
-                                     const Scan& sc, const Method& mt,
-                                     long long p, double* c, int* base,
-                                     unsigned& mask, int& w, unsigned& flags) {
-  // c = s Cgd V(p)
-  double Vp[kMaxGate];
+// Voltage of pixel p at gate g.
+__device__ __forceinline__ double scan_voltage(const Scan& sc, int ng, long long p,
+                                               int g) {
   if (sc.kind == 0) {
     const int ix = (int)(p % sc.W), iy = (int)(p / sc.W);
-    const double xs = sc.x0 + ix * sc.dx, ys = sc.y0 + iy * sc.dy;
-    for (int g = 0; g < ng; ++g) Vp[g] = sc.V0[g] + xs * sc.u[g] + ys * sc.w[g];
-  } else {
-    for (int g = 0; g < ng; ++g) Vp[g] = sc.V[p * ng + g];
+    return sc.V0[g] + (sc.x0 + ix * sc.dx) * sc.u[g] + (sc.y0 + iy * sc.dy) * sc.w[g];
   }
-  for (int i = 0; i < n; ++i) {
-    double a = 0.0;
-    for (int g = 0; g < ng; ++g) a += md->Cgd[i * ng + g] * Vp[g];
-    c[i] = mt.carrier * a;
-  }
+  return sc.V[p * ng + g];
+}
+
+// c_i = s (Cgd V(p))_i in FP64
+__device__ __forceinline__ double pixel_c_f64(const ModelData* md, int ng,
+                                              const Scan& sc, double carrier,
+                                              long long p, int i) {
+  double a = 0.0;
+  for (int g = 0; g < ng; ++g) a += md->Cgd[i * ng + g] * scan_voltage(sc, ng, p, g);
+  return carrier * a;
+}
+
+// Continuous minimum and candidate set in FP64 from a given c (one thread).
+__device__ inline int settle_pixel_f64(const ModelData* md, int n, const Method& mt,
+                                       const double* c, int* base, unsigned& mask,
+                                       int& w, unsigned& flags) {
   double x[kMaxDot];
   const bool closed = mt.closed != 0;
   unsigned A = 0u;
@@ -225,6 +230,14 @@ __device__ inline int prep_pixel_f64(const ModelData* md, int n, int ng,
     }
   }
   return candidate_set_f64(n, x, mt.t, closed, mt.n_charges, base, mask, w, flags);
+}
+
+__device__ inline int prep_pixel_f64(const ModelData* md, int n, int ng,
+                                     const Scan& sc, const Method& mt,
+                                     long long p, double* c, int* base,
+                                     unsigned& mask, int& w, unsigned& flags) {
+  for (int i = 0; i < n; ++i) c[i] = pixel_c_f64(md, ng, sc, mt.carrier, p, i);
+  return settle_pixel_f64(md, n, mt, c, base, mask, w, flags);
 }
 
 }  // namespace qa

@@ -227,10 +227,13 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
       gm[m] = e;
     }
     const int popo = __popc(o);
+    const int nsteps = 1 << nmid;  // Gray steps that stay inside the k slots
 #pragma unroll
     for (int s = 0; s < NM; ++s) {
+      // Guarded rather than `break`: the walk must stay fully unrolled so that
+      // every flip position below is a compile-time register index.
+      if (s >= nsteps) continue;
       if (s > 0) {
-        if (s >= (1 << nmid)) break;
         const int mb = ctz_c((unsigned)s);
         const bool up = (gray_c((unsigned)s) >> mb) & 1u;
         A = up ? A + gm[mb] : A - gm[mb];

@@ -405,8 +405,10 @@ static cudaError_t run_soft(const SoftLaunch& a, cudaStream_t st) {
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
+  if (a.ev) cudaEventRecord(a.ev[0], st);
   k_soft<L1, L2, CLOSED, BWD, KMAX><<<grid, kSoftThreads, smem, st>>>(a);
   if (BWD) k_soft_finalize<<<1, 256, 0, st>>>(a, (int)grid);
+  if (a.ev) cudaEventRecord(a.ev[1], st);
   return cudaGetLastError();
 }
 
