@@ -107,7 +107,8 @@ typedef struct {
     long long unresolved;      /* pixels the recheck could not settle         */
     long long overflow;        /* pixels whose charges exceed int8            */
     long long doubled;         /* closed pixels whose threshold was doubled   */
-    long long shortlist_max;   /* largest FP64 shortlist in the recheck       */
+    long long shortlist_max;   /* largest near-tie shortlist (blocks)         */
+    long long resolved;        /* near ties settled by exact double-float    */
     int team;                  /* lanes per pixel used by the search kernel   */
     int inner_bits;            /* unrolled inner / middle bits of the search  */
     int middle_bits;

@@ -56,7 +56,8 @@ class qa_raster(ctypes.Structure):
 class qa_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_longlong) for n in (
         "pixels", "candidates", "evaluated", "qp_pixels", "flagged", "near_tie",
-        "boundary", "unresolved", "overflow", "doubled", "shortlist_max")] + [
+        "boundary", "unresolved", "overflow", "doubled", "shortlist_max",
+        "resolved")] + [
         ("team", ctypes.c_int), ("inner_bits", ctypes.c_int),
         ("middle_bits", ctypes.c_int), ("timed", ctypes.c_int),
         ("ms_prep", ctypes.c_double), ("ms_search", ctypes.c_double),
@@ -68,7 +69,9 @@ _SYMBOLS = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The in-tree library, or the one named by QARRAY_LIB (a build made
+    elsewhere)."""
+    return os.environ.get("QARRAY_LIB") or _build.LIB
 
 
 def load():
@@ -76,7 +79,7 @@ def load():
     global _lib, _SYMBOLS
     if _lib is not None:
         return _lib
-    path = _build.build()
+    path = os.environ.get("QARRAY_LIB") or _build.build()
     lib = ctypes.CDLL(path)
     P = ctypes.c_void_p
     D = ctypes.POINTER(ctypes.c_double)

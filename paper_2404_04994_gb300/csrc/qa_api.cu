@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/qarray.h"
+#include "qarray.h"
 #include "qa_launch.h"
 
 namespace {
@@ -101,9 +101,42 @@ struct qa_model {
   bool timing = false;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int last_kind = 0;  // 1 ground state, 2 soft
+  qa::BlockCounts* d_bc_prep = nullptr;
+  qa::BlockCounts* d_bc_search = nullptr;
+  int n_bc_prep = 0, n_bc_search = 0;
 };
 
 namespace {
+
+qa::df split(double v) {
+  const float hi = (float)v;
+  return {hi, (float)(v - (double)hi)};
+}
+
+// FP32 / double-float forms of the model used by every kernel.
+void fill_consts(int n, qa::ModelData* md) {
+  qa::ModelConsts& k = md->k;
+  std::memset(&k, 0, sizeof(k));
+  double tot = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double r = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const qa::df m = split(md->M[i * n + j]);
+      k.Mhi[i * qa::kLdM + j] = m.hi;
+      k.Mlo[i * qa::kLdM + j] = m.lo;
+      k.Cdd[i * qa::kLdM + j] = (float)md->Cdd[i * n + j];
+      r += md->Cdd[i * n + j];
+    }
+    k.sv[i] = (float)r;
+    k.vs[i] = split(md->vs[i]);
+    tot += r;
+  }
+  k.s_s = (float)tot;
+  // decision margin of an FP32 QP minimum: 8 cond(Cdd) (n + 1) u32 per unit
+  // of (1 + max|c| + N_hat)
+  k.bx_qp_scale = (float)(8.0 * md->cond * (n + 1) * 5.9604644775390625e-8);
+  k.model_bad = md->status != 0;
+}
 
 // Validate + convert host matrices into a ModelData (Maxwell form).
 int build_model(int n, int ng, int form, const double* Cdd_in,
@@ -156,6 +189,7 @@ int build_model(int n, int ng, int form, const double* Cdd_in,
   for (int i = 0; i < n; ++i) md->vs[i] /= s;
   md->cond = norm1(n, md->Cdd) * norm1(n, md->M);
   md->status = 0;
+  fill_consts(n, md);
   return QA_OK;
 }
 
@@ -206,6 +240,29 @@ qa::SearchCfg choose_cfg(int n, double t, long long P, int num_sms) {
          (1 << spare) >= 4 * c.T)
     c.T *= 2;
   return c;
+}
+
+// c0 = s Cgd (V0 + x0 u + y0 w), du = s Cgd u dx, dw = s Cgd w dy in FP64 on
+// the host, split into double-float; only when the host copy is current.
+qa::RasterK raster_constants(const qa_model* m, const qa::Scan& sc) {
+  qa::RasterK rk;
+  std::memset(&rk, 0, sizeof(rk));
+  if (sc.kind != 0 || m->host_stale) return rk;
+  const int n = m->n, ng = m->ng;
+  for (int i = 0; i < n; ++i) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int g = 0; g < ng; ++g) {
+      const double G = m->carrier * m->host.Cgd[i * ng + g];
+      a += G * (sc.V0[g] + sc.x0 * sc.u[g] + sc.y0 * sc.w[g]);
+      b += G * (sc.u[g] * sc.dx);
+      c += G * (sc.w[g] * sc.dy);
+    }
+    rk.c0[i] = split(a);
+    rk.du[i] = split(b);
+    rk.dw[i] = split(c);
+  }
+  rk.valid = 1;
+  return rk;
 }
 
 int prep_team(int n) {
@@ -268,16 +325,27 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
   if ((rc = select_device(m))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const long long P = sc.P;
+  const size_t Pn = (size_t)(P > 0 ? P : 1);
+  const size_t nbp = (size_t)P + 1, nbs = (size_t)P + 1;  // >= block counts
   const size_t off_list = align_up(sizeof(qa::Counters), 256);
-  const size_t off_recs = align_up(off_list + sizeof(int) * (size_t)(P > 0 ? P : 1), 256);
-  const size_t total = off_recs + sizeof(qa::PixRec) * (size_t)(P > 0 ? P : 1);
+  const size_t off_tie = align_up(off_list + sizeof(int) * Pn, 256);
+  const size_t off_bcp = align_up(off_tie + sizeof(qa::TieEntry) * Pn, 256);
+  const size_t off_bcs = align_up(off_bcp + sizeof(qa::BlockCounts) * nbp, 256);
+  const size_t off_recs = align_up(off_bcs + sizeof(qa::BlockCounts) * nbs, 256);
+  const size_t total = off_recs + sizeof(qa::PixRec) * Pn;
   if ((rc = ensure_workspace(m, total))) return rc;
   char* ws = (char*)m->ws;
   m->d_cnt = (qa::Counters*)ws;
-  cudaError_t e = cudaMemsetAsync(m->d_cnt, 0, sizeof(qa::Counters), st);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   m->last_P = P;
-  if (P == 0) return QA_OK;
+  m->n_bc_prep = m->n_bc_search = 0;
+  m->d_bc_prep = (qa::BlockCounts*)(ws + off_bcp);
+  m->d_bc_search = (qa::BlockCounts*)(ws + off_bcs);
+  if (P == 0) {
+    cudaError_t e0 = cudaMemsetAsync(m->d_cnt, 0, sizeof(qa::Counters), st);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "cudaMemsetAsync");
+    return QA_OK;
+  }
+  cudaError_t e;
 
   qa::GsLaunch a;
   std::memset(&a, 0, sizeof(a));
@@ -291,10 +359,14 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
   a.mt.carrier = m->carrier;
   a.cfg = choose_cfg(m->n, t, P, m->num_sms);
   a.prep_team = prep_team(m->n);
+  a.rk = raster_constants(m, sc);
   a.bx_analytic = 4.0e-7f;
   a.bx_qp_scale = 0.f;  // derived from the device model's condition number
   a.recs = (qa::PixRec*)(ws + off_recs);
   a.flag_list = (int*)(ws + off_list);
+  a.tie_list = (qa::TieEntry*)(ws + off_tie);
+  a.bc_prep = m->d_bc_prep;
+  a.bc_search = m->d_bc_search;
   a.cnt = m->d_cnt;
   a.out_n = out_n;
   a.out_U = out_U;
@@ -304,6 +376,8 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
   m->last_P = P;
   a.ev = m->timing ? m->ev : nullptr;
   m->last_kind = 1;
+  m->n_bc_prep = qa::prep_blocks(a);
+  m->n_bc_search = qa::search_blocks(a);
   e = qa::launch_ground_state(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "ground-state launch");
   return QA_OK;
@@ -334,15 +408,17 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
   else if (m->n <= 8) cfg = {5, 4, 8};
   else cfg = {5, 4, 32};
   const size_t off_list = align_up(sizeof(qa::Counters), 256);
-  const size_t off_recs = align_up(off_list + sizeof(int) * (size_t)P, 256);
+  const size_t off_bcp = align_up(off_list + sizeof(int) * (size_t)P, 256);
+  const size_t off_recs = align_up(off_bcp + sizeof(qa::BlockCounts) * ((size_t)P + 1), 256);
   const size_t off_part = align_up(off_recs + sizeof(qa::PixRec) * (size_t)P, 256);
   const size_t total =
       off_part + (bwd ? sizeof(float) * qa::soft_partials_floats(m->n, P, cfg) : 0);
   if ((rc = ensure_workspace(m, total))) return rc;
   char* ws = (char*)m->ws;
   m->d_cnt = (qa::Counters*)ws;
-  cudaError_t e = cudaMemsetAsync(m->d_cnt, 0, sizeof(qa::Counters), st);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  m->d_bc_prep = (qa::BlockCounts*)(ws + off_bcp);
+  m->n_bc_search = 0;
+  cudaError_t e;
 
   qa::GsLaunch g;
   std::memset(&g, 0, sizeof(g));
@@ -356,12 +432,15 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
   g.mt.carrier = m->carrier;
   g.cfg = cfg;
   g.prep_team = prep_team(m->n);
+  g.rk = raster_constants(m, sc);
   g.bx_analytic = 4.0e-7f;
   g.recs = (qa::PixRec*)(ws + off_recs);
   g.flag_list = (int*)(ws + off_list);
+  g.bc_prep = m->d_bc_prep;
   g.cnt = m->d_cnt;
   g.num_sms = m->num_sms;
   if (m->timing) cudaEventRecord(m->ev[0], st);
+  m->n_bc_prep = qa::prep_blocks(g);
   e = qa::launch_prep(g, st);
   if (e != cudaSuccess) return cuda_fail(e, "prep launch");
 
@@ -559,6 +638,32 @@ int qa_model_stats(qa_model* m, void* stream, qa_stats* out) {
   qa::Counters c;
   e = cudaMemcpy(&c, m->d_cnt, sizeof(c), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "counters read");
+  // per-block counters: summed here, in block order
+  std::vector<qa::BlockCounts> bc;
+  if (m->n_bc_prep > 0) {
+    bc.resize((size_t)m->n_bc_prep);
+    e = cudaMemcpy(bc.data(), m->d_bc_prep, sizeof(qa::BlockCounts) * bc.size(),
+                   cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "block counters read");
+    for (const auto& b : bc) {
+      c.candidates += b.candidates;
+      c.qp += b.qp;
+      c.doubled += b.doubled;
+    }
+  }
+  if (m->n_bc_search > 0) {
+    bc.resize((size_t)m->n_bc_search);
+    e = cudaMemcpy(bc.data(), m->d_bc_search, sizeof(qa::BlockCounts) * bc.size(),
+                   cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "block counters read");
+    for (const auto& b : bc) {
+      c.evaluated += b.evaluated;
+      c.near_tie += b.near_tie;
+      c.boundary += b.boundary;
+      c.overflow += b.overflow;
+    }
+  }
+  c.flagged = c.near_tie + c.boundary;
   out->candidates = (long long)c.candidates;
   out->evaluated = (long long)c.evaluated;
   out->qp_pixels = (long long)c.qp;
@@ -569,6 +674,7 @@ int qa_model_stats(qa_model* m, void* stream, qa_stats* out) {
   out->overflow = (long long)c.overflow;
   out->doubled = (long long)c.doubled;
   out->shortlist_max = (long long)c.shortlist_max;
+  out->resolved = (long long)c.resolved;
   out->pixels = m->last_P;
   if (m->timing && m->last_kind != 0) {
     float t0 = 0.f, t1 = 0.f, t2 = 0.f;

@@ -90,8 +90,23 @@ struct __align__(16) PixRec {
   float bound;          // FP32 gap below which the pixel is a near-tie
 };
 
+// FP32 / double-float constants of a model, derived once from the FP64
+// matrices whenever they change (host set-up or the device Cholesky) and
+// staged by every block with plain 16-byte loads.
+struct __align__(16) ModelConsts {
+  float Mhi[kMaxDot * kLdM];   // M = Cdd^-1 as double-float (hi, lo)
+  float Mlo[kMaxDot * kLdM];
+  float Cdd[kMaxDot * kLdM];   // FP32 Cdd for the QP
+  float sv[kMaxDot];           // Cdd 1
+  df vs[kMaxDot];              // Cdd 1 / (1^T Cdd 1)   (Appendix D)
+  float s_s;                   // 1^T Cdd 1
+  float bx_qp_scale;           // QP decision margin per unit of (1+|c|+N_hat)
+  int model_bad;               // device Cholesky of an updated Cdd failed
+  int pad;
+};
+
 // Device copy of a model (written by the host or by the Cholesky kernel).
-struct ModelData {
+struct __align__(16) ModelData {
   double Cdd[kMaxDot * kMaxDot];
   double M[kMaxDot * kMaxDot];        // Cdd^-1
   double Cgd[kMaxDot * kMaxGate];
@@ -99,6 +114,7 @@ struct ModelData {
   double cond;                        // ||Cdd||_1 ||M||_1
   int status;                         // 0 ok; nonzero: Cdd not PD on update
   int pad;
+  ModelConsts k;                      // FP32 forms of the above
 };
 
 // Where the voltages come from: a raster (by value) or a device list.
@@ -111,6 +127,14 @@ struct Scan {
   const double* V;   // points: [P, n_gate]
 };
 
+// Raster induced-charge constants c0, du, dw (double-float), computed on the
+// host when the host copy of the model is current.
+struct RasterK {
+  int valid;
+  int pad;
+  df c0[kMaxDot], du[kMaxDot], dw[kMaxDot];
+};
+
 struct Method {
   double t;          // threshold
   int closed;
@@ -120,9 +144,31 @@ struct Method {
 
 struct Counters {
   unsigned long long candidates, evaluated, qp, flagged, near_tie, boundary,
-      unresolved, overflow, doubled, shortlist_max;
-  unsigned int n_flag;  // length of the recheck list
-  unsigned int pad;
+      unresolved, overflow, doubled, shortlist_max, resolved;
+  unsigned int n_flag;  // length of the FP64 recheck list
+  unsigned int n_tie;   // length of the near-tie list
+};
+
+// A near-tie pixel and the FP32 minimum its search found.
+struct TieEntry {
+  int p;
+  float m1;
+};
+
+// Copy the model's FP32 constants into shared memory (16-byte vectors).
+__device__ __forceinline__ void stage_consts(const ModelConsts* g, ModelConsts* s) {
+  const int4* src = reinterpret_cast<const int4*>(g);
+  int4* dst = reinterpret_cast<int4*>(s);
+  constexpr int nvec = (int)(sizeof(ModelConsts) / sizeof(int4));
+  for (int i = threadIdx.x; i < nvec; i += blockDim.x) dst[i] = src[i];
+}
+
+// Per-block counters written without atomics (summed on the host on demand).
+struct BlockCounts {
+  unsigned long long candidates;  // prep: admissible candidates
+  unsigned long long evaluated;   // search: candidate energies evaluated
+  unsigned int qp, doubled;       // prep
+  unsigned int near_tie, boundary, overflow, pad;  // search
 };
 
 // ---------------------------------------------------------------------------

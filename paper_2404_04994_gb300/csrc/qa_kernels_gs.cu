@@ -10,6 +10,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPrepThreads = 128;
 constexpr int kSearchThreads = 128;
 constexpr int kRecheckThreads = 128;
+constexpr int kResolveThreads = 256;
 constexpr int kRecheckL1 = 4, kRecheckL2 = 3;  // 2^9 outer states at k = 16
 constexpr unsigned kBcap = 1024;
 
@@ -21,31 +22,42 @@ __device__ __forceinline__ unsigned long long binom(int k, int w) {
   return r;
 }
 
-// Load M (double-float split), Cdd (FP32), Cdd 1 and 1^T Cdd 1 into smem.
-__device__ inline void stage_model(const ModelData* md, int n, float* sMhi,
-                                   float* sMlo, float* sCdd, float* sv,
-                                   float* s_s) {
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    if (sMhi) {
-      const df m = df_from_double(md->M[e]);
-      sMhi[i * kLdM + j] = m.hi;
-      if (sMlo) sMlo[i * kLdM + j] = m.lo;
-    }
-    if (sCdd) sCdd[i * kLdM + j] = __double2float_rn(md->Cdd[e]);
+// ---------------------------------------------------------------------------
+// (a0) raster constants of a block: c(ix, iy) = c0 + ix du + iy dw with
+// c0 = s Cgd (V0 + x0 u + y0 w), du = s Cgd u dx, dw = s Cgd w dy, formed in
+// double-float FP32 from FP64 inputs (one FP64 rounding per input, no FP64
+// dependency chains: FP64 issues at a small fraction of the FP32 rate here).
+// ---------------------------------------------------------------------------
+__device__ inline void raster_consts(const ModelData* md, int n, int ng, const Scan& sc,
+                                     double carrier, df* sV, df* sU, df* sW, df* c0,
+                                     df* du, df* dw) {
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+    sV[g] = df_from_double(sc.V0[g] + sc.x0 * sc.u[g] + sc.y0 * sc.w[g]);
+    sU[g] = df_from_double(sc.u[g] * sc.dx);
+    sW[g] = df_from_double(sc.w[g] * sc.dy);
   }
-  if (sv) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      double r = 0.0;
-      for (int j = 0; j < n; ++j) r += md->Cdd[i * n + j];
-      sv[i] = __double2float_rn(r);
-    }
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int e = 0; e < n * n; ++e) s += md->Cdd[e];
-      *s_s = __double2float_rn(s);
-    }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 3 * n; e += blockDim.x) {
+    const int i = e % n, which = e / n;
+    const df* vec = which == 0 ? sV : (which == 1 ? sU : sW);
+    df acc = {0.f, 0.f};
+    for (int g = 0; g < ng; ++g)
+      acc = df_add(acc, df_mul(df_from_double(carrier * md->Cgd[i * ng + g]), vec[g]));
+    (which == 0 ? c0 : (which == 1 ? du : dw))[i] = acc;
   }
+}
+
+// Block sum of per-thread counts (all threads must call; result in thread 0).
+template <typename U>
+__device__ __forceinline__ U block_sum(U v, U* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  U t = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
 }
 
 // ---------------------------------------------------------------------------
@@ -57,24 +69,31 @@ __device__ inline void stage_model(const ModelData* md, int n, float* sMhi,
 // ---------------------------------------------------------------------------
 template <bool CLOSED>
 __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch a) {
-  __shared__ float sMhi[kMaxDot * kLdM], sMlo[kMaxDot * kLdM],
-      sCdd[kMaxDot * kLdM];
-  __shared__ float sv[kMaxDot];
-  __shared__ float s_s;
-  __shared__ df sc0[kMaxDot], sdu[kMaxDot], sdw[kMaxDot], svs[kMaxDot];
+  __shared__ ModelConsts cs;
+  __shared__ df sV[kMaxGate], sU[kMaxGate], sW[kMaxGate];
+  __shared__ df sc0[kMaxDot], sdu[kMaxDot], sdw[kMaxDot];
   __shared__ float sx[kPrepThreads];
   __shared__ int sst[kPrepThreads];
+  __shared__ unsigned long long red64[kPrepThreads / 32];
+  __shared__ unsigned red32[kPrepThreads / 32];
   const int n = a.n;
-  stage_model(a.md, n, sMhi, sMlo, sCdd, sv, &s_s);
-  if (a.sc.kind == 0) raster_setup(a.md, n, a.ng, a.sc, a.mt.carrier, sc0, sdu, sdw);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) svs[i] = df_from_double(a.md->vs[i]);
+  stage_consts(&a.md->k, &cs);
+  if (a.sc.kind == 0) {
+    if (a.rk.valid) {
+      if (threadIdx.x < kMaxDot) {
+        sc0[threadIdx.x] = a.rk.c0[threadIdx.x];
+        sdu[threadIdx.x] = a.rk.du[threadIdx.x];
+        sdw[threadIdx.x] = a.rk.dw[threadIdx.x];
+      }
+    } else {
+      raster_consts(a.md, n, a.ng, a.sc, a.mt.carrier, sV, sU, sW, sc0, sdu, sdw);
+    }
+  }
   __syncthreads();
-  // decision margin of an FP32 QP minimum: 8 cond(Cdd) (n + 1) u32 per unit
-  // of (1 + max|c| + N_hat)
-  const float bx_qp_scale =
-      a.bx_qp_scale > 0.f ? a.bx_qp_scale
-                          : 8.f * (float)a.md->cond * (float)(n + 1) * 5.9604645e-8f;
-  const bool model_bad = a.md->status != 0;
+  const float* sMhi = cs.Mhi;
+  const float* sMlo = cs.Mlo;
+  const float bx_qp_scale = a.bx_qp_scale > 0.f ? a.bx_qp_scale : cs.bx_qp_scale;
+  const bool model_bad = cs.model_bad != 0;
 
   const int TP = a.prep_team;
   const int lt = threadIdx.x & (TP - 1);
@@ -110,8 +129,6 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch a) {
   };
   auto tballot = [&](bool pred) { return (__ballot_sync(tmask, pred) & tmask) >> tbase; };
 
-  if (!active) return;  // whole teams retire together
-
   // (a1) c_i
   df c = {0.f, 0.f};
   if (live) {
@@ -125,9 +142,9 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch a) {
   // (a2) analytic continuous minimum (Appendix C / D)
   df x = c;
   if (CLOSED) {
-    const df cs = tsum_df(c);
-    const df lam = df_sub({(float)nhat, 0.f}, cs);  // N_hat <= 2^24
-    if (live) x = df_add(c, df_mul(lam, svs[lt]));
+    const df csum = tsum_df(c);
+    const df lam = df_sub({(float)nhat, 0.f}, csum);  // N_hat <= 2^24
+    if (live) x = df_add(c, df_mul(lam, cs.vs[lt]));
   }
   const unsigned A =
       tballot(live && (x.hi < 0.f || (x.hi == 0.f && x.lo < 0.f)));
@@ -146,8 +163,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch a) {
       if (lt == 0) {
         float cf[kMaxDot], xf[kMaxDot];
         for (int j = 0; j < n; ++j) cf[j] = sx[threadIdx.x + j];
-        const int st = qp_active_set<float>(n, sCdd, kLdM, cf, CLOSED, (float)nhat, sv,
-                                            s_s, A, 0.25f * bx_qp_scale * scale,
+        const int st = qp_active_set<float>(n, cs.Cdd, kLdM, cf, CLOSED, (float)nhat,
+                                            cs.sv, cs.s_s, A, 0.25f * bx_qp_scale * scale,
                                             4 * n + 4, xf);
         for (int j = 0; j < n; ++j) sx[threadIdx.x + j] = xf[j];
         sst[threadIdx.x] = st;
@@ -213,26 +230,34 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch a) {
   const float S = tsum_f(Si);
   const int k = __popc(mask);
 
-  PixRec* rec = a.recs + p;
+  PixRec* rec = a.recs + (active ? p : 0);
   if (live) {
     rec->h[lt] = h;
     rec->chi[lt] = c.hi;
     rec->clo[lt] = c.lo;
     rec->base[lt] = (short)base;
   }
-  unsigned long long my_cand = 0, my_qp = 0, my_doubled = 0;
-  if (lt == 0) {
+  unsigned long long my_cand = 0;
+  unsigned my_qp = 0, my_doubled = 0;
+  if (active && lt == 0) {
     rec->mask = (unsigned short)mask;
     rec->k = (unsigned char)k;
     rec->w = (signed char)(CLOSED ? w : -1);
     rec->flags = (unsigned char)flags;
     rec->bound = near_tie_bound(S, k, a.cfg.L2);
     my_cand = CLOSED ? binom(k, w) : (1ull << k);
-    my_qp = (flags & kFlagQP) ? 1 : 0;
-    my_doubled = (flags & kFlagDoubled) ? 1 : 0;
-    if (my_cand) atomicAdd(&a.cnt->candidates, my_cand);
-    if (my_qp) atomicAdd(&a.cnt->qp, my_qp);
-    if (my_doubled) atomicAdd(&a.cnt->doubled, my_doubled);
+    my_qp = (flags & kFlagQP) ? 1u : 0u;
+    my_doubled = (flags & kFlagDoubled) ? 1u : 0u;
+  }
+  __syncwarp();
+  const unsigned long long bc = block_sum(my_cand, red64);
+  const unsigned bq = block_sum(my_qp, red32);
+  const unsigned bd = block_sum(my_doubled, red32);
+  if (threadIdx.x == 0) {
+    BlockCounts& o = a.bc_prep[blockIdx.x];
+    o.candidates = bc;
+    o.qp = bq;
+    o.doubled = bd;
   }
 }
 
@@ -241,12 +266,16 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch a) {
 // ---------------------------------------------------------------------------
 template <int L1, int L2, bool CLOSED>
 __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch a) {
-  __shared__ float sM[kMaxDot * kLdM], sMlo[kMaxDot * kLdM];
+  __shared__ ModelConsts cs;
   __shared__ int sdot[kSearchThreads][kMaxDot];
   __shared__ float sh[kSearchThreads][kMaxDot];
+  __shared__ unsigned long long red64[kSearchThreads / 32];
+  __shared__ unsigned red32[kSearchThreads / 32];
   const int n = a.n;
-  stage_model(a.md, n, sM, sMlo, nullptr, nullptr, nullptr);
+  stage_consts(&a.md->k, &cs);
   __syncthreads();
+  const float* sM = cs.Mhi;
+  const float* sMlo = cs.Mlo;
 
   const int T = a.cfg.T;
   const int team = threadIdx.x / T, lt = threadIdx.x % T;
@@ -310,39 +339,183 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch a) {
     u = df_add(u, o);
     flags |= __shfl_xor_sync(kFull, flags, off);
   }
-  unsigned long long my_nt = 0, my_bd = 0, my_fl = 0, my_ov = 0;
+  unsigned my_nt = 0, my_bd = 0, my_ov = 0;
   if (active) {
     flags |= rec->flags;
     if (!(m2 - m1 > rec->bound)) flags |= kFlagNearTie;
     if (lt == 0) {
       if (a.out_U) a.out_U[p] = 0.5 * df_to_double(u);
-      if (flags & (kFlagNearTie | kFlagBoundary | kFlagQPCap)) {
+      if (flags & (kFlagBoundary | kFlagQPCap | kFlagUnresolved)) {
+        // the candidate set itself may be wrong: FP64 recheck
         const unsigned at = atomicAdd(&a.cnt->n_flag, 1u);
         a.flag_list[at] = (int)p;
-        my_fl = 1;
-        my_nt = (flags & kFlagNearTie) ? 1 : 0;
-        my_bd = (flags & (kFlagBoundary | kFlagQPCap)) ? 1 : 0;
+        my_bd = 1;
+      } else if (flags & kFlagNearTie) {
+        // right set, uncertain order: exact energies of the close candidates
+        const unsigned at = atomicAdd(&a.cnt->n_tie, 1u);
+        a.tie_list[at] = TieEntry{(int)p, m1};
+        my_nt = 1;
       }
-      my_ov = (flags & kFlagOverflow) ? 1 : 0;
+      my_ov = (flags & kFlagOverflow) ? 1u : 0u;
       if (a.out_flags) a.out_flags[p] = (uint8_t)flags;
     }
   }
-  for (int off = 16; off > 0; off >>= 1) {
-    ev += __shfl_xor_sync(kFull, ev, off);
-    my_nt += __shfl_xor_sync(kFull, my_nt, off);
-    my_bd += __shfl_xor_sync(kFull, my_bd, off);
-    my_fl += __shfl_xor_sync(kFull, my_fl, off);
-    my_ov += __shfl_xor_sync(kFull, my_ov, off);
+  const unsigned long long bev = block_sum(ev, red64);
+  const unsigned bnt = block_sum(my_nt, red32);
+  const unsigned bbd = block_sum(my_bd, red32);
+  const unsigned bov = block_sum(my_ov, red32);
+  if (threadIdx.x == 0) {
+    BlockCounts& o = a.bc_search[blockIdx.x];
+    o.evaluated = bev;
+    o.near_tie = bnt;
+    o.boundary = bbd;
+    o.overflow = bov;
   }
-  if ((threadIdx.x & 31) == 0) {
-    if (ev) atomicAdd(&a.cnt->evaluated, ev);
-    if (my_fl) {
-      atomicAdd(&a.cnt->flagged, my_fl);
-      atomicAdd(&a.cnt->near_tie, my_nt);
-      atomicAdd(&a.cnt->boundary, my_bd);
+}
+
+// ---------------------------------------------------------------------------
+// (a7, near ties): a pixel whose candidate set is certain but whose FP32
+// best/runner-up gap is under the error bound.  One warp per pixel re-walks
+// the candidates collecting every block whose FP32 minimum is within the
+// bound of the search's minimum (the exact argmin is guaranteed to be among
+// them) and evaluates those candidates exactly, relative to the base state,
+//     E(b) = sum_{s in b} (h_s + M_ss / 2) + sum_{s < s' in b} M_ss',
+// in double-float arithmetic with h = M (base - c) in double-float (about
+// 1e-13 absolute).  No FP64 instructions: GB300's FP64 rate is a small
+// fraction of its FP32 rate.  A pixel whose two best exact energies are
+// within 1e-10 (a true tie) or whose list overflows goes on to the FP64
+// recheck, which also applies the lexicographic tie rule.
+// ---------------------------------------------------------------------------
+template <int L1, int L2, bool CLOSED>
+__global__ void __launch_bounds__(kResolveThreads) k_resolve(GsLaunch a) {
+  constexpr int NI = 1 << L1;
+  constexpr int NM = 1 << L2;
+  constexpr int NW = kResolveThreads / 32;
+  constexpr unsigned kCap = 128;
+  __shared__ ModelConsts cs;
+  __shared__ int sdot[kMaxDot];
+  __shared__ float sh[kMaxDot];
+  __shared__ df shd[kMaxDot];
+  __shared__ df sui[kMaxDot];
+  __shared__ unsigned blist[kCap];
+  __shared__ unsigned bcnt;
+  __shared__ df rbest[NW], rsec[NW];
+  __shared__ unsigned rbits[NW];
+  stage_consts(&a.md->k, &cs);
+  __syncthreads();
+  const float* sM = cs.Mhi;
+  const float* sMlo = cs.Mlo;
+  const int n = a.n;
+  const unsigned ntie = a.cnt->n_tie;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  unsigned my_res = 0;
+  for (unsigned it = blockIdx.x; it < ntie; it += gridDim.x) {
+    const TieEntry te = a.tie_list[it];
+    const long long p = te.p;
+    const PixRec* rec = a.recs + p;
+    const unsigned mask = rec->mask;
+    const int k = __popc(mask);
+    const int w = rec->w;
+    // h_i = (M (base - c))_i in double-float, and U(base) = r0 . h / 2
+    if (tid < n) {
+      df hi = {0.f, 0.f};
+      for (int j = 0; j < n; ++j) {
+        const df rj = df_sub({(float)rec->base[j], 0.f}, {rec->chi[j], rec->clo[j]});
+        hi = df_add(hi, df_mul({sM[tid * kLdM + j], sMlo[tid * kLdM + j]}, rj));
+      }
+      const df r0 = df_sub({(float)rec->base[tid], 0.f}, {rec->chi[tid], rec->clo[tid]});
+      sui[tid] = df_mul(hi, r0);
+      if ((mask >> tid) & 1u) {
+        const int s = __popc(mask & ((1u << tid) - 1u));
+        sdot[s] = tid;
+        sh[s] = rec->h[tid];
+        shd[s] = df_add(hi, df_mul_f({sM[tid * kLdM + tid], sMlo[tid * kLdM + tid]}, 0.5f));
+      }
     }
-    if (my_ov) atomicAdd(&a.cnt->overflow, my_ov);
+    if (tid == 0) bcnt = 0u;
+    __syncthreads();
+    // every block whose FP32 minimum is within the bound of the search's
+    const SlotView sv{sdot, sh, k, w};
+    const float thr = te.m1 + rec->bound;
+    float d1, d2;
+    unsigned db;
+    unsigned long long ev = 0;
+    search_lane<L1, L2, CLOSED, true>(sM, sv, tid, kResolveThreads, thr, blist, &bcnt,
+                                      kCap, d1, db, d2, ev);
+    __syncthreads();
+    const unsigned nb = bcnt;
+    const bool fits = nb <= kCap;
+    df best = {kInf, 0.f}, second = {kInf, 0.f};
+    unsigned bbits = 0xffffffffu;
+    if (fits) {
+      for (unsigned idx = tid; idx < nb * NI; idx += kResolveThreads) {
+        const unsigned id = blist[idx / NI];
+        const unsigned b = idx % NI;
+        const unsigned bits = ((id >> L2) << (L1 + L2)) | ((id & (NM - 1)) << L1) | b;
+        if ((bits >> k) != 0u) continue;
+        if (CLOSED && __popc(bits) != w) continue;
+        df E = {0.f, 0.f};
+        for (unsigned m = bits; m; m &= m - 1u) {
+          const int s = __ffs(m) - 1;
+          const int d = sdot[s];
+          E = df_add(E, shd[s]);
+          for (unsigned q = bits & ((1u << s) - 1u); q; q &= q - 1u) {
+            const int d2i = sdot[__ffs(q) - 1];
+            E = df_add(E, {sM[d * kLdM + d2i], sMlo[d * kLdM + d2i]});
+          }
+        }
+        const bool better = E.hi < best.hi || (E.hi == best.hi && E.lo < best.lo) ||
+                            (E.hi == best.hi && E.lo == best.lo && __brev(bits) < __brev(bbits));
+        if (better) { second = best; best = E; bbits = bits; }
+        else if (E.hi < second.hi || (E.hi == second.hi && E.lo < second.lo)) { second = E; }
+      }
+    }
+    auto less = [](df x, df y) { return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo); };
+    auto merge = [&](df ob, df os, unsigned obb) {
+      const bool take = less(ob, best) ||
+                        (ob.hi == best.hi && ob.lo == best.lo && __brev(obb) < __brev(bbits));
+      const df lose = take ? best : ob;
+      const df s2 = less(os, second) ? os : second;
+      second = less(lose, s2) ? lose : s2;
+      if (take) { best = ob; bbits = obb; }
+    };
+    for (int off = 16; off > 0; off >>= 1) {
+      df ob, os;
+      ob.hi = __shfl_xor_sync(kFull, best.hi, off);
+      ob.lo = __shfl_xor_sync(kFull, best.lo, off);
+      os.hi = __shfl_xor_sync(kFull, second.hi, off);
+      os.lo = __shfl_xor_sync(kFull, second.lo, off);
+      merge(ob, os, __shfl_xor_sync(kFull, bbits, off));
+    }
+    if (lane == 0) { rbest[wid] = best; rsec[wid] = second; rbits[wid] = bbits; }
+    __syncthreads();
+    if (tid == 0) {
+      for (int i = 1; i < NW; ++i) merge(rbest[i], rsec[i], rbits[i]);
+      df ub = {0.f, 0.f};
+      for (int i = 0; i < n; ++i) ub = df_add(ub, sui[i]);
+      ub = df_mul_f(ub, 0.5f);
+      const double gap = df_to_double(second) - df_to_double(best);
+      const double eps = 1e-10 * (1.0 + fabs(df_to_double(ub)));
+      if (!fits || bbits == 0xffffffffu || !(gap > eps)) {
+        const unsigned at = atomicAdd(&a.cnt->n_flag, 1u);
+        a.flag_list[at] = (int)p;
+      } else {
+        unsigned flags = (a.out_flags ? a.out_flags[p] : 0u) | kFlagRechecked;
+        for (int i = 0; i < n; ++i) {
+          int ni = rec->base[i];
+          if ((mask >> i) & 1u) ni += (int)((bbits >> __popc(mask & ((1u << i) - 1u))) & 1u);
+          if (ni > 127) { ni = 127; flags |= kFlagOverflow; }
+          a.out_n[p * n + i] = (int8_t)ni;
+        }
+        if (a.out_U) a.out_U[p] = df_to_double(df_add(ub, best));
+        if (a.out_flags) a.out_flags[p] = (uint8_t)flags;
+        my_res += 1;
+      }
+      atomicMax(&a.cnt->shortlist_max, (unsigned long long)nb);
+    }
+    __syncthreads();
   }
+  if (tid == 0 && my_res) atomicAdd(&a.cnt->resolved, (unsigned long long)my_res);
 }
 
 // ---------------------------------------------------------------------------
@@ -376,8 +549,7 @@ __global__ void __launch_bounds__(kRecheckThreads) k_recheck(GsLaunch a) {
   __shared__ unsigned blist[kBcap];
   __shared__ unsigned bcount;
   const int n = a.n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x)
-    sM[(e / n) * kLdM + (e % n)] = __double2float_rn(a.md->M[e]);
+  for (int e = threadIdx.x; e < kMaxDot * kLdM; e += blockDim.x) sM[e] = a.md->k.Mhi[e];
   __syncthreads();
   const unsigned nflag = a.cnt->n_flag;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
@@ -517,31 +689,36 @@ __global__ void __launch_bounds__(kRecheckThreads) k_recheck(GsLaunch a) {
 // ---------------------------------------------------------------------------
 // host-side dispatch
 // ---------------------------------------------------------------------------
+int prep_blocks(const GsLaunch& a) {
+  const long long tpb = kPrepThreads / a.prep_team;
+  return (int)((a.sc.P + tpb - 1) / tpb);
+}
+int search_blocks(const GsLaunch& a) {
+  const int teams = kSearchThreads / a.cfg.T;
+  return (int)((a.sc.P + teams - 1) / teams);
+}
+
 template <int L1, int L2, bool CLOSED>
 static cudaError_t run(const GsLaunch& a, cudaStream_t st) {
-  const long long P = a.sc.P;
-  const long long tpb = kPrepThreads / a.prep_team;
-  const unsigned gp = (unsigned)((P + tpb - 1) / tpb);
   if (a.ev) cudaEventRecord(a.ev[0], st);
-  k_prep<CLOSED><<<gp, kPrepThreads, 0, st>>>(a);
+  cudaMemsetAsync(a.cnt, 0, sizeof(Counters), st);
+  k_prep<CLOSED><<<prep_blocks(a), kPrepThreads, 0, st>>>(a);
   if (a.ev) cudaEventRecord(a.ev[1], st);
-  const int teams = kSearchThreads / a.cfg.T;
-  const unsigned gs = (unsigned)((P + teams - 1) / teams);
-  k_search<L1, L2, CLOSED><<<gs, kSearchThreads, 0, st>>>(a);
+  k_search<L1, L2, CLOSED><<<search_blocks(a), kSearchThreads, 0, st>>>(a);
   if (a.ev) cudaEventRecord(a.ev[2], st);
-  k_recheck<CLOSED><<<2 * a.num_sms, kRecheckThreads, 0, st>>>(a);
+  k_resolve<L1, L2, CLOSED><<<a.num_sms, kResolveThreads, 0, st>>>(a);
+  k_recheck<CLOSED><<<a.num_sms, kRecheckThreads, 0, st>>>(a);
   if (a.ev) cudaEventRecord(a.ev[3], st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_prep(const GsLaunch& a, cudaStream_t st) {
-  const long long tpb = kPrepThreads / a.prep_team;
-  const unsigned gp = (unsigned)((a.sc.P + tpb - 1) / tpb);
-  if (gp == 0) return cudaSuccess;
+  cudaMemsetAsync(a.cnt, 0, sizeof(Counters), st);
+  if (a.sc.P == 0) return cudaGetLastError();
   if (a.mt.closed)
-    k_prep<true><<<gp, kPrepThreads, 0, st>>>(a);
+    k_prep<true><<<prep_blocks(a), kPrepThreads, 0, st>>>(a);
   else
-    k_prep<false><<<gp, kPrepThreads, 0, st>>>(a);
+    k_prep<false><<<prep_blocks(a), kPrepThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

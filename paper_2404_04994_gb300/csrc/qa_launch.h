@@ -20,25 +20,31 @@ struct GsLaunch {
   const ModelData* md;
   int n, ng;
   Scan sc;
+  RasterK rk;          // host-computed raster constants (rk.valid = 0: device)
   Method mt;
   SearchCfg cfg;
   int prep_team;       // lanes per pixel in the prep kernel (pow2 >= n, <= 16)
   float bx_analytic;   // decision margin for double-float continuous minima
   float bx_qp_scale;   // ... times (1 + max|c| + N_hat) for FP32 QP minima
   PixRec* recs;        // scratch [P]
-  int* flag_list;      // scratch [P]
-  Counters* cnt;       // scratch, zeroed by the caller
+  int* flag_list;      // scratch [P]: pixels for the FP64 recheck
+  TieEntry* tie_list;  // scratch [P]: near-tie pixels for the resolve kernel
+  Counters* cnt;       // scratch, zeroed at the start of each call
+  BlockCounts* bc_prep;    // scratch [prep blocks]
+  BlockCounts* bc_search;  // scratch [search blocks]
   int8_t* out_n;
   double* out_U;
   uint8_t* out_flags;
   int num_sms;
-  cudaEvent_t* ev;     // optional: 4 events recorded around prep/search/recheck
+  cudaEvent_t* ev;     // optional: events around setup+prep / search / resolve+recheck
 };
 
-// prep -> search -> FP64 recheck, enqueued on `st`.
+// setup -> prep -> search -> resolve -> FP64 recheck, enqueued on `st`.
 cudaError_t launch_ground_state(const GsLaunch& a, cudaStream_t st);
-// prep alone (continuous minimum + candidate set records), for the soft path.
+// prep alone (candidate-set records), for the soft path.
 cudaError_t launch_prep(const GsLaunch& a, cudaStream_t st);
+int prep_blocks(const GsLaunch& a);
+int search_blocks(const GsLaunch& a);
 bool search_cfg_supported(const SearchCfg& c);
 
 struct SoftLaunch {

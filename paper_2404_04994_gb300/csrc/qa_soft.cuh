@@ -61,16 +61,14 @@ __device__ __forceinline__ float delta_energy(const TeamSlots& ts, const float* 
 // Soft occupation (forward) and, with BWD, the per-block gradient partials.
 template <int L1, int L2, bool CLOSED, bool BWD, int KMAX>
 __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
-  __shared__ float sM[kMaxDot * kLdM], sMlo[kMaxDot * kLdM];
+  __shared__ ModelConsts cs;
   __shared__ TeamSlots tsm[kSoftThreads / 4 > 0 ? kSoftThreads / 4 : 1];
   extern __shared__ float s_contrib[];  // BWD: [teams][contrib_len]
   const int n = a.n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const df m = df_from_double(a.md->M[e]);
-    sM[(e / n) * kLdM + (e % n)] = m.hi;
-    sMlo[(e / n) * kLdM + (e % n)] = m.lo;
-  }
+  stage_consts(&a.md->k, &cs);
   __syncthreads();
+  const float* sM = cs.Mhi;
+  const float* sMlo = cs.Mlo;
   const int T = a.cfg.T;  // >= 4
   const int team = threadIdx.x / T, lt = threadIdx.x % T;
   const int teams = blockDim.x / T;

@@ -40,7 +40,10 @@ __global__ void k_model_update(ModelData* md, int n, int ng, const double* Cdd,
     md->status = ok ? 0 : 1;
   }
   __syncthreads();
-  if (!ok) return;
+  if (!ok) {
+    if (tid == 0) md->k.model_bad = 1;
+    return;
+  }
   if (tid < n) {
     const int col = tid;
     double z[kMaxDot], y[kMaxDot];
@@ -81,6 +84,31 @@ __global__ void k_model_update(ModelData* md, int n, int ng, const double* Cdd,
       n1m = fmax(n1m, sm);
     }
     md->cond = n1c * n1m;
+  }
+  __syncthreads();
+  // FP32 / double-float forms (same definitions as the host set-up)
+  ModelConsts& k = md->k;
+  for (int e = tid; e < kMaxDot * kLdM; e += blockDim.x) {
+    const int i = e / kLdM, j = e % kLdM;
+    const bool live = i < n && j < n;
+    const df m = live ? df_from_double(md->M[i * n + j]) : df{0.f, 0.f};
+    k.Mhi[e] = m.hi;
+    k.Mlo[e] = m.lo;
+    k.Cdd[e] = live ? __double2float_rn(md->Cdd[i * n + j]) : 0.f;
+  }
+  if (tid < kMaxDot) {
+    double r = 0.0;
+    for (int j = 0; j < n && tid < n; ++j) r += md->Cdd[tid * n + j];
+    k.sv[tid] = __double2float_rn(r);
+    k.vs[tid] = tid < n ? df_from_double(md->vs[tid]) : df{0.f, 0.f};
+  }
+  if (tid == 0) {
+    double tot = 0.0;
+    for (int e = 0; e < n * n; ++e) tot += md->Cdd[e];
+    k.s_s = __double2float_rn(tot);
+    k.bx_qp_scale = __double2float_rn(8.0 * md->cond * (n + 1) * 5.9604644775390625e-8);
+    k.model_bad = md->status != 0;
+    k.pad = 0;
   }
 }
 
