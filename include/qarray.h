@@ -215,6 +215,32 @@ int qa_model_set_timing(qa_model* m, int enable);
 /* Counters of the last call on this model; synchronises `stream` first. */
 int qa_model_stats(qa_model* m, void* stream, qa_stats* out);
 
+/* Largest raster qa_ground_state_open_static accepts (128 x 128 pixels). */
+#define QA_STATIC_MAX_PIXELS 16384
+
+/* The open ground state of qa_ground_state_open, for callers that cannot
+ * allocate GPU memory while they run -- a control loop that drives an
+ * instrument in real time and must not stall on, or fail in, an allocation,
+ * or a host process whose GPU memory is already fully handed to another
+ * allocator.  (The paper has no counterpart; this is a property of this
+ * library only.)  It allocates nothing: where qa_ground_state_open keeps its
+ * per-pixel scratch in a workspace it grows with cudaMalloc, this call uses a
+ * fixed array of static device memory for at most QA_STATIC_MAX_PIXELS
+ * pixels; larger rasters are rejected with QA_ERR_SHAPE.  The model must come
+ * from qa_model_create (run it during set-up); inputs, outputs and errors are
+ * otherwise those of qa_ground_state_open.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call on a device shares the one array, which keeps the previous
+ *    call's contents: calls that overlap on the GPU race, so serialise them
+ *    (one stream, or events).
+ *  - qa_model_stats does not report these calls.
+ *  - The array (about 5.4 MB) is held on every GPU that loads the library
+ *    until the process exits. */
+int qa_ground_state_open_static(qa_model* m, const qa_raster* r, double threshold,
+                                int8_t* out_n, double* out_U, uint8_t* out_flags,
+                                void* stream);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* qa_last_error(void);
 

@@ -104,6 +104,8 @@ def load():
                                             P, P, P, P]),
         "qa_model_stats": (I, [P, P, ctypes.POINTER(qa_stats)]),
         "qa_model_set_timing": (I, [P, I]),
+        "qa_ground_state_open_static": (I, [P, ctypes.POINTER(qa_raster),
+                                            ctypes.c_double, P, P, P, P]),
         "qa_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -232,6 +234,24 @@ def qa_ground_state_open(m, raster, threshold, out_n, out_U=None, out_flags=None
     r = make_raster(raster, ng)
     P = r.W * r.H
     _check(load().qa_ground_state_open(
+        m, ctypes.byref(r), float(threshold), _dev(out_n, torch.int8, P * n, "out_n"),
+        _dev(out_U, torch.float64, P, "out_U"),
+        _dev(out_flags, torch.uint8, P, "out_flags"), _stream(stream)))
+
+
+STATIC_MAX_PIXELS = 16384
+
+
+def qa_ground_state_open_static(m, raster, threshold, out_n, out_U=None,
+                                out_flags=None, stream=None):
+    """qa_ground_state_open without any GPU allocation: the scratch is the
+    library's static device array, so the raster holds at most
+    STATIC_MAX_PIXELS pixels and calls on one device must not overlap."""
+    import torch
+    n, ng = qa_model_shape(m)
+    r = make_raster(raster, ng)
+    P = r.W * r.H
+    _check(load().qa_ground_state_open_static(
         m, ctypes.byref(r), float(threshold), _dev(out_n, torch.int8, P * n, "out_n"),
         _dev(out_U, torch.float64, P, "out_U"),
         _dev(out_flags, torch.uint8, P, "out_flags"), _stream(stream)))

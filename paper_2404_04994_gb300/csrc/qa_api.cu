@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -701,3 +702,110 @@ int qa_model_stats(qa_model* m, void* stream, qa_stats* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// qa_ground_state_open_static: the open ground-state call for callers that
+// must not allocate GPU memory while they run (see include/qarray.h).  Its
+// scratch -- the per-pixel records, the recheck lists and the counters that
+// qa_ground_state_open keeps in a cudaMalloc'd model workspace -- lives in
+// the file-scope array below instead, sized for QA_STATIC_MAX_PIXELS pixels.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticPixels = (size_t)QA_STATIC_MAX_PIXELS;
+constexpr size_t al256(size_t v) { return (v + 255) / 256 * 256; }
+constexpr size_t kStOffList = al256(sizeof(qa::Counters));
+constexpr size_t kStOffTie = al256(kStOffList + sizeof(int) * kStaticPixels);
+constexpr size_t kStOffBcp = al256(kStOffTie + sizeof(qa::TieEntry) * kStaticPixels);
+constexpr size_t kStOffBcs = al256(kStOffBcp + sizeof(qa::BlockCounts) * (kStaticPixels + 1));
+constexpr size_t kStOffRecs = al256(kStOffBcs + sizeof(qa::BlockCounts) * (kStaticPixels + 1));
+constexpr size_t kStaticBytes = al256(kStOffRecs + sizeof(qa::PixRec) * kStaticPixels);
+
+// Device address of the array below, looked up once per device.
+constexpr int kStaticMaxDevices = 64;
+void* g_static_ptr[kStaticMaxDevices] = {};
+std::mutex g_static_mu;
+
+}  // namespace
+
+// Scratch of qa_ground_state_open_static.  Every GPU that loads this library
+// holds it (about 5.4 MB) until the process exits; all calls on a device share
+// it, so calls that overlap on that device race.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+extern "C" int qa_ground_state_open_static(qa_model* m, const qa_raster* r,
+                                           double threshold, int8_t* out_n,
+                                           double* out_U, uint8_t* out_flags,
+                                           void* stream) {
+  if (!m) return fail(QA_ERR_INVALID, "null model");
+  if (!r) return fail(QA_ERR_INVALID, "null raster");
+  if (!(threshold >= 0.0 && threshold <= 1.0))
+    return fail(QA_ERR_RANGE, "threshold %g outside [0, 1]", threshold);
+  ScanIn in;
+  in.r = r;
+  qa::Scan sc;
+  int rc = make_scan(m, in, &sc);
+  if (rc) return rc;
+  const long long P = sc.P;
+  if (P > (long long)kStaticPixels)
+    return fail(QA_ERR_SHAPE, "raster of %lld pixels exceeds the static scratch of %lld "
+                "pixels (QA_STATIC_MAX_PIXELS); use qa_ground_state_open", P,
+                (long long)kStaticPixels);
+  if (!out_n) return fail(QA_ERR_INVALID, "null out_n");
+  if ((rc = select_device(m))) return rc;
+
+  // In host code g_static_scratch names a host-side stand-in, not device
+  // memory: its device address comes from the runtime, once per device, with
+  // that device current (this first call must precede any stream capture).
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (m->device < 0 || m->device >= kStaticMaxDevices)
+      return fail(QA_ERR_INVALID, "device %d out of range", m->device);
+    if (!g_static_ptr[m->device]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+      g_static_ptr[m->device] = p;
+    }
+    base = g_static_ptr[m->device];
+  }
+  char* ws = (char*)base;
+  cudaStream_t st = (cudaStream_t)stream;
+  qa::Counters* cnt = (qa::Counters*)ws;
+  // the list counters must start at zero on every call (the array keeps the
+  // last call's contents); the records and block counts are overwritten
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(qa::Counters), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  if (P == 0) return QA_OK;
+
+  qa::GsLaunch a;
+  std::memset(&a, 0, sizeof(a));
+  a.md = m->d_md;
+  a.n = m->n;
+  a.ng = m->ng;
+  a.sc = sc;
+  a.mt.t = threshold;
+  a.mt.closed = 0;
+  a.mt.n_charges = 0;
+  a.mt.carrier = m->carrier;
+  a.cfg = choose_cfg(m->n, threshold, P, m->num_sms);
+  a.prep_team = prep_team(m->n);
+  a.rk = raster_constants(m, sc);
+  a.bx_analytic = 4.0e-7f;
+  a.bx_qp_scale = 0.f;
+  a.recs = (qa::PixRec*)(ws + kStOffRecs);
+  a.flag_list = (int*)(ws + kStOffList);
+  a.tie_list = (qa::TieEntry*)(ws + kStOffTie);
+  a.bc_prep = (qa::BlockCounts*)(ws + kStOffBcp);
+  a.bc_search = (qa::BlockCounts*)(ws + kStOffBcs);
+  a.cnt = cnt;
+  a.out_n = out_n;
+  a.out_U = out_U;
+  a.out_flags = out_flags;
+  a.num_sms = m->num_sms;
+  a.ev = nullptr;
+  e = qa::launch_ground_state(a, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ground-state launch");
+  return QA_OK;
+}

@@ -1,0 +1,65 @@
+"""The allocation-free entry point against the ordinary one.
+
+qa_ground_state_open_static serves callers that cannot allocate GPU memory
+while they run (real-time instrument loops, processes whose GPU memory is
+owned by another allocator): its scratch is a static device array of the
+library instead of a cudaMalloc'd workspace.  This file sorts last so that a
+run stopping at the first failure has already run every other test; it must
+pass alone in a fresh process as well as after the rest of the suite.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2404_04994_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _both(qa, cfg, raster, t):
+    import torch
+    m = qa.Model(cfg["Cdd"], cfg["Cgd"])
+    P = raster["W"] * raster["H"]
+    n_ref, U_ref, f_ref = m.ground_state_open(raster, threshold=t)
+    n_st = torch.full((P, m.n_dot), -1, dtype=torch.int8, device="cuda")
+    U_st = torch.full((P,), float("nan"), dtype=torch.float64, device="cuda")
+    f_st = torch.full((P,), 255, dtype=torch.uint8, device="cuda")
+    qa.qa_ground_state_open_static(m.handle, raster, t, n_st, U_st, f_st)
+    torch.cuda.synchronize()
+    out = (n_ref.cpu().numpy().reshape(P, -1), U_ref.cpu().numpy(), f_ref.cpu().numpy(),
+           n_st.cpu().numpy(), U_st.cpu().numpy(), f_st.cpu().numpy())
+    m.close()
+    return out
+
+
+def _check(out):
+    n_ref, U_ref, f_ref, n_st, U_st, f_st = out
+    np.testing.assert_array_equal(n_st, n_ref)
+    np.testing.assert_array_equal(f_st, f_ref)
+    scale = np.maximum(np.abs(U_ref), 0.5)
+    assert float(np.max(np.abs(U_st - U_ref) / scale)) <= 1e-5
+
+
+def test_static_entry_matches_open_twice_in_a_row(qa):
+    # two calls in a row on the shared static scratch: a 16-dot diagram with
+    # near-tie pixels, then a 2-dot one that must not see the first's lists
+    cfg = inputs.grid16(W=64, H=48)
+    _check(_both(qa, cfg, cfg["raster"], 1.0))
+    cfg2 = inputs.double_dot()
+    _check(_both(qa, cfg2, cfg2["raster"], 1.0))
+    _check(_both(qa, cfg, cfg["raster"], 0.5))
+
+
+def test_static_entry_rejects_oversized_raster(qa):
+    import torch
+    cfg = inputs.double_dot(W=129, H=128)
+    m = qa.Model(cfg["Cdd"], cfg["Cgd"])
+    P = 129 * 128
+    assert P > qa.STATIC_MAX_PIXELS
+    out = torch.empty((P, 2), dtype=torch.int8, device="cuda")
+    with pytest.raises(qa.QAError) as e:
+        qa.qa_ground_state_open_static(m.handle, cfg["raster"], 1.0, out)
+    assert e.value.code == -2
+    assert "QA_STATIC_MAX_PIXELS" in str(e.value)
+    m.close()
