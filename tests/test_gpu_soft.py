@@ -1,0 +1,160 @@
+"""GPU parity of the finite-temperature occupation (Sec. IV.B) and its
+gradient against the FP64 oracle and central finite differences."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_04994_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+MEAN_TOL = 1e-5        # absolute, on <n>
+GRAD_RTOL = 1e-4       # relative to the largest gradient entry
+
+
+def _soft_gpu(qa, cfg, kT, t=1.0, closed=False, n_charges=0, raster=None):
+    ras = cfg["raster"] if raster is None else raster
+    m = qa.Model(cfg["Cdd"], cfg["Cgd"])
+    mean, logZ = m.soft_occupation(ras, kT, threshold=t, closed=closed, n_charges=n_charges)
+    out = mean.cpu().numpy().astype(np.float64), logZ.cpu().numpy().astype(np.float64)
+    m.close()
+    return out
+
+
+@pytest.mark.parametrize("kT", [0.01, 0.05])
+def test_soft_grid8_full_raster(qa, kT):
+    cfg = inputs.grid8(kT=kT)
+    mean, logZ = _soft_gpu(qa, cfg, kT)
+    om, ol = oracle.soft(cfg["Cdd"], cfg["Cgd"], raster=cfg["raster"], kT=kT)
+    err = np.abs(mean - om).max()
+    assert err <= MEAN_TOL, err
+    rel = np.abs(logZ - ol) / np.maximum(1.0, np.abs(ol))
+    assert rel.max() <= 1e-5, rel.max()
+
+
+@pytest.mark.parametrize("closed", [False, True])
+@pytest.mark.parametrize("t", [1.0, 0.4])
+def test_soft_chain4(qa, closed, t):
+    cfg = inputs.chain4(W=60, H=50, closed=closed)
+    kT = 0.02
+    mean, logZ = _soft_gpu(qa, cfg, kT, t=t, closed=closed, n_charges=4)
+    om, ol = oracle.soft(cfg["Cdd"], cfg["Cgd"], raster=cfg["raster"], kT=kT, t=t,
+                         closed=closed, n_charges=4)
+    assert np.abs(mean - om).max() <= MEAN_TOL
+    if closed:
+        np.testing.assert_allclose(mean.sum(1), 4.0, atol=1e-5)
+
+
+def test_soft_sixteen_dots_small(qa):
+    cfg = inputs.grid16(W=6, H=5)
+    kT = 0.05
+    mean, _ = _soft_gpu(qa, cfg, kT)
+    om, _ = oracle.soft(cfg["Cdd"], cfg["Cgd"], raster=cfg["raster"], kT=kT)
+    assert np.abs(mean - om).max() <= MEAN_TOL
+
+
+def _grad_gpu(qa, cfg, kT, gbar, raster=None, t=1.0, closed=False, n_charges=0):
+    import torch
+    ras = cfg["raster"] if raster is None else raster
+    m = qa.Model(cfg["Cdd"], cfg["Cgd"])
+    n, ng = m.n_dot, m.n_gate
+    g = torch.tensor(gbar, dtype=torch.float32, device="cuda").contiguous()
+    dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    dG = torch.empty((n, ng), dtype=torch.float64, device="cuda")
+    qa.qa_soft_occupation_backward(m.handle, ras, kT, t, closed, n_charges, g, dC, dG)
+    out = dC.cpu().numpy(), dG.cpu().numpy()
+    m.close()
+    return out
+
+
+@pytest.mark.parametrize("kT", [0.01, 0.05])
+def test_gradient_matches_oracle(qa, kT):
+    cfg = inputs.grid8(W=48, H=40, kT=kT)
+    P = 48 * 40
+    gbar = np.random.Generator(np.random.PCG64(5)).normal(size=(P, 8))
+    dC, dG = _grad_gpu(qa, cfg, kT, gbar)
+    _, oC, oG = oracle.soft_grad(cfg["Cdd"], cfg["Cgd"], gbar, raster=cfg["raster"], kT=kT)
+    sc = max(np.abs(oC).max(), np.abs(oG).max())
+    assert np.abs(dC - oC).max() <= GRAD_RTOL * sc
+    assert np.abs(dG - oG).max() <= GRAD_RTOL * sc
+    np.testing.assert_allclose(dC, dC.T, atol=1e-12 * sc)
+
+
+def test_gradient_closed_and_threshold(qa):
+    cfg = inputs.chain4(W=30, H=20, closed=True)
+    kT = 0.03
+    gbar = np.random.Generator(np.random.PCG64(6)).normal(size=(600, 4))
+    dC, dG = _grad_gpu(qa, cfg, kT, gbar, t=0.5, closed=True, n_charges=4)
+    _, oC, oG = oracle.soft_grad(cfg["Cdd"], cfg["Cgd"], gbar, raster=cfg["raster"],
+                                 kT=kT, t=0.5, closed=True, n_charges=4)
+    sc = max(np.abs(oC).max(), np.abs(oG).max())
+    assert np.abs(dC - oC).max() <= GRAD_RTOL * sc
+    assert np.abs(dG - oG).max() <= GRAD_RTOL * sc
+
+
+def test_gradient_matches_central_differences(qa):
+    # FD of the FP64 oracle forward (h = 1e-4) on the loss L = sum g . <n>,
+    # restricted to pixels whose continuous minimum stays well inside its
+    # cell, so the frozen candidate set is the set at every perturbed point.
+    cfg = inputs.grid8(W=20, H=16, kT=0.05)
+    kT, h = 0.05, 1e-4
+    ras = cfg["raster"]
+    P = 20 * 16
+    xs = np.linspace(ras["x0"], ras["x1"], 20)
+    ys = np.linspace(ras["y0"], ras["y1"], 16)
+    V = np.array([ras["V0"] + xs[p % 20] * ras["u"] + ys[p // 20] * ras["w"] for p in range(P)])
+    keep = []
+    for p in range(P):
+        x, qp, _ = oracle.continuous_min(cfg["Cdd"], V[p] @ cfg["Cgd"].T)
+        fr = np.maximum(x, 0) - np.floor(np.maximum(x, 0))
+        keep.append(not qp and (np.minimum(fr, 1 - fr) > 0.02).all())
+    keep = np.array(keep)
+    gbar = np.random.Generator(np.random.PCG64(7)).normal(size=(P, 8))
+    gbar[~keep] = 0.0
+    dC, dG = _grad_gpu(qa, cfg, kT, gbar)
+
+    def loss(Cdd, Cgd):
+        mean, _ = oracle.soft(Cdd, Cgd, V=V[keep], kT=kT)
+        return float((mean * gbar[keep]).sum())
+
+    sc = max(np.abs(dC).max(), np.abs(dG).max())
+    rng = np.random.Generator(np.random.PCG64(8))
+    for _ in range(6):
+        i, j = rng.integers(0, 8, 2)
+        E = np.zeros((8, 8))
+        E[i, j] = E[j, i] = 1.0
+        fd = (loss(cfg["Cdd"] + h * E, cfg["Cgd"]) - loss(cfg["Cdd"] - h * E, cfg["Cgd"])) / (2 * h)
+        an = dC[i, j] + (dC[j, i] if i != j else 0.0)
+        assert abs(an - fd) <= 1e-4 * sc + 1e-5 * abs(fd), (i, j, an, fd)
+        E = np.zeros((8, 8))
+        E[i, j] = 1.0
+        fd = (loss(cfg["Cdd"], cfg["Cgd"] + h * E) - loss(cfg["Cdd"], cfg["Cgd"] - h * E)) / (2 * h)
+        assert abs(dG[i, j] - fd) <= 1e-4 * sc + 1e-5 * abs(fd), (i, j, dG[i, j], fd)
+
+
+def test_autograd_function_and_fit_loop(qa):
+    import torch
+    from paper_2404_04994_gb300 import autograd as qag
+    cfg = inputs.grid8(W=40, H=40, kT=0.05)
+    kT = 0.05
+    target = qag.target_diagram(cfg["Cdd_target"], cfg["Cgd_target"], cfg["raster"], kT)
+    fit = qag.CapacitanceFit(cfg["Cdd"], cfg["Cgd"], cfg["raster"], target, kT, lr=2e-3)
+    losses = []
+    for _ in range(30):
+        fit.step()
+        losses.append(float(fit.loss))
+    fit.close()
+    assert np.isfinite(losses).all()
+    assert losses[-1] < 0.7 * losses[1], losses[:3] + losses[-3:]
+    # the Function's gradient equals the backward kernel's
+    Cdd = torch.tensor(cfg["Cdd"], device="cuda", requires_grad=True)
+    Cgd = torch.tensor(cfg["Cgd"], device="cuda", requires_grad=True)
+    m = qa.Model(cfg["Cdd"], cfg["Cgd"])
+    ras = inputs.grid8(W=12, H=10)["raster"]
+    mean = qag.soft_occupation(Cdd, Cgd, m.handle, ras, kT)
+    gbar = torch.randn_like(mean)
+    (mean * gbar).sum().backward()
+    dC, dG = _grad_gpu(qa, cfg, kT, gbar.cpu().numpy(), raster=ras)
+    np.testing.assert_allclose(Cdd.grad.cpu().numpy(), dC, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(Cgd.grad.cpu().numpy(), dG, rtol=1e-9, atol=1e-12)
+    m.close()
