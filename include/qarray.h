@@ -215,6 +215,47 @@ int qa_model_set_timing(qa_model* m, int enable);
 /* Counters of the last call on this model; synchronises `stream` first. */
 int qa_model_stats(qa_model* m, void* stream, qa_stats* out);
 
+/* One array of a batched call (qa_batch_create). */
+typedef struct {
+    qa_model* model;      /* from qa_model_create; all models on one device   */
+    qa_raster raster;     /* host vectors, read by qa_batch_create            */
+    double threshold;     /* Eq. "threshold", [0, 1]                          */
+    int closed;           /* 0 open, 1 closed with n_charges carriers         */
+    int n_charges;
+    int team;             /* lanes per pixel of the search (1..32, power of
+                             two); 0 = the library's choice                   */
+    int8_t* out_n;        /* DEVICE [H, W, n_dot]                              */
+    double* out_U;        /* DEVICE [H, W] (nullable)                          */
+    uint8_t* out_flags;   /* DEVICE [H, W] (nullable)                          */
+} qa_batch_item;
+
+typedef struct qa_batch qa_batch;
+
+/* Prepare a batch of `count` independent arrays of any dot count, raster size
+ * and open/closed form: validates every item (as the single-array calls do),
+ * uploads one descriptor per array, builds the work-unit queues (runs of
+ * pixels of one array, ordered by estimated cost, largest first) and
+ * allocates the scratch (per-pixel records for all pixels, the recheck lists).
+ * Synchronous; *out is owned by the caller (qa_batch_destroy).  The models
+ * and output buffers must outlive the batch; model capacitances may change
+ * between runs only through qa_model_update (same shapes).
+ * Errors: as qa_ground_state_open, plus QA_ERR_SHAPE for count < 1 or items on
+ * different devices. */
+int qa_batch_create(const qa_batch_item* items, int count, qa_batch** out);
+
+/* Run the batch on `stream`: one persistent prep launch and one persistent
+ * search launch whose blocks take work units from a device queue, then the
+ * near-tie and FP64 recheck kernels over all arrays.  Asynchronous, allocates
+ * nothing and synchronises nothing, so it can be captured in a CUDA graph.
+ * Runs of one batch must not overlap on the GPU. */
+int qa_batch_run(qa_batch* b, void* stream);
+
+/* Counters of the last run (synchronises `stream`). */
+int qa_batch_stats(qa_batch* b, void* stream, qa_stats* out);
+
+/* Release the batch (synchronises the device). */
+int qa_batch_destroy(qa_batch* b);
+
 /* Largest raster qa_ground_state_open_static accepts (128 x 128 pixels). */
 #define QA_STATIC_MAX_PIXELS 16384
 

@@ -64,6 +64,14 @@ class qa_stats(ctypes.Structure):
         ("ms_recheck", ctypes.c_double), ("ms_soft", ctypes.c_double)]
 
 
+class qa_batch_item(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_void_p), ("raster", qa_raster),
+                ("threshold", ctypes.c_double), ("closed", ctypes.c_int),
+                ("n_charges", ctypes.c_int), ("team", ctypes.c_int),
+                ("out_n", ctypes.c_void_p), ("out_U", ctypes.c_void_p),
+                ("out_flags", ctypes.c_void_p)]
+
+
 _lib = None
 _SYMBOLS = None
 
@@ -106,6 +114,10 @@ def load():
         "qa_model_set_timing": (I, [P, I]),
         "qa_ground_state_open_static": (I, [P, ctypes.POINTER(qa_raster),
                                             ctypes.c_double, P, P, P, P]),
+        "qa_batch_create": (I, [ctypes.POINTER(qa_batch_item), I, ctypes.POINTER(P)]),
+        "qa_batch_run": (I, [P, P]),
+        "qa_batch_stats": (I, [P, P, ctypes.POINTER(qa_stats)]),
+        "qa_batch_destroy": (I, [P]),
         "qa_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -381,3 +393,92 @@ class Model:
 
     def stats(self, stream=None):
         return qa_model_stats(self.handle, stream)
+
+
+# --------------------------------------------------------------------------
+# batched calls
+# --------------------------------------------------------------------------
+
+def qa_batch_create(items):
+    """items: list of dicts {model (handle), raster, threshold, closed,
+    n_charges, team, out_n, out_U, out_flags} (torch CUDA outputs).  Returns
+    (handle, keep) -- keep holds the host rasters until the call returns."""
+    import torch
+    arr = (qa_batch_item * len(items))()
+    keep = []
+    for i, it in enumerate(items):
+        n, ng = qa_model_shape(it["model"])
+        r = make_raster(it["raster"], ng)
+        keep.append(r)
+        P = r.W * r.H
+        arr[i].model = it["model"].value if isinstance(it["model"], ctypes.c_void_p) else it["model"]
+        arr[i].raster = r
+        arr[i].threshold = float(it.get("threshold", 1.0))
+        arr[i].closed = int(bool(it.get("closed", False)))
+        arr[i].n_charges = int(it.get("n_charges", 0))
+        arr[i].team = int(it.get("team", 0))
+        arr[i].out_n = _dev(it["out_n"], torch.int8, P * n, "out_n")
+        arr[i].out_U = _dev(it.get("out_U"), torch.float64, P, "out_U")
+        arr[i].out_flags = _dev(it.get("out_flags"), torch.uint8, P, "out_flags")
+    h = ctypes.c_void_p()
+    _check(load().qa_batch_create(arr, len(items), ctypes.byref(h)))
+    return h
+
+
+def qa_batch_run(b, stream=None):
+    _check(load().qa_batch_run(b, _stream(stream)))
+
+
+def qa_batch_stats(b, stream=None):
+    s = qa_stats()
+    _check(load().qa_batch_stats(b, _stream(stream), ctypes.byref(s)))
+    return {f[0]: getattr(s, f[0]) for f in qa_stats._fields_}
+
+
+def qa_batch_destroy(b):
+    _check(load().qa_batch_destroy(b))
+
+
+class Batch:
+    """A prepared batch of arrays with device outputs allocated per array.
+
+    specs: list of dicts {Cdd, Cgd, raster, threshold, closed, n_charges,
+    team}.  outputs[i] = (n [H, W, N] int8, U [H, W] f64, flags [H, W] u8)."""
+
+    def __init__(self, specs):
+        import torch
+        self.models, self.outputs, items = [], [], []
+        for sp in specs:
+            m = Model(sp["Cdd"], sp["Cgd"])
+            self.models.append(m)
+            H, W = int(sp["raster"]["H"]), int(sp["raster"]["W"])
+            n = torch.empty((H, W, m.n_dot), dtype=torch.int8, device="cuda")
+            U = torch.empty((H, W), dtype=torch.float64, device="cuda")
+            f = torch.empty((H, W), dtype=torch.uint8, device="cuda")
+            self.outputs.append((n, U, f))
+            items.append(dict(model=m.handle, raster=sp["raster"],
+                              threshold=sp.get("threshold", sp.get("t", 1.0)),
+                              closed=sp.get("closed", False), n_charges=sp.get("n_charges", 0),
+                              team=sp.get("team", 0), out_n=n, out_U=U, out_flags=f))
+        self.handle = qa_batch_create(items)
+        self.pixels = sum(int(sp["raster"]["H"]) * int(sp["raster"]["W"]) for sp in specs)
+
+    def run(self, stream=None):
+        qa_batch_run(self.handle, stream)
+
+    def stats(self, stream=None):
+        return qa_batch_stats(self.handle, stream)
+
+    def close(self):
+        if self.handle is not None:
+            qa_batch_destroy(self.handle)
+            self.handle = None
+        for m in self.models:
+            m.close()
+        self.models = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

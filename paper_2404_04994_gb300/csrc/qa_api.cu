@@ -3,6 +3,7 @@
 // Argument validation, the FP64 model set-up (Cholesky inverse of Cdd,
 // Appendix B positive-definiteness check), workspace management and kernel
 // dispatch.  No pixel work happens on the host.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -329,8 +330,8 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
   const size_t Pn = (size_t)(P > 0 ? P : 1);
   const size_t nbp = (size_t)P + 1, nbs = (size_t)P + 1;  // >= block counts
   const size_t off_list = align_up(sizeof(qa::Counters), 256);
-  const size_t off_tie = align_up(off_list + sizeof(int) * Pn, 256);
-  const size_t off_bcp = align_up(off_tie + sizeof(qa::TieEntry) * Pn, 256);
+  const size_t off_tie = align_up(off_list + sizeof(qa::ListEntry) * Pn, 256);
+  const size_t off_bcp = align_up(off_tie + sizeof(qa::ListEntry) * Pn, 256);
   const size_t off_bcs = align_up(off_bcp + sizeof(qa::BlockCounts) * nbp, 256);
   const size_t off_recs = align_up(off_bcs + sizeof(qa::BlockCounts) * nbs, 256);
   const size_t total = off_recs + sizeof(qa::PixRec) * Pn;
@@ -350,30 +351,31 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
 
   qa::GsLaunch a;
   std::memset(&a, 0, sizeof(a));
-  a.md = m->d_md;
-  a.n = m->n;
-  a.ng = m->ng;
-  a.sc = sc;
-  a.mt.t = t;
-  a.mt.closed = closed ? 1 : 0;
-  a.mt.n_charges = closed ? n_charges : 0;
-  a.mt.carrier = m->carrier;
-  a.cfg = choose_cfg(m->n, t, P, m->num_sms);
-  a.prep_team = prep_team(m->n);
-  a.rk = raster_constants(m, sc);
-  a.bx_analytic = 4.0e-7f;
-  a.bx_qp_scale = 0.f;  // derived from the device model's condition number
-  a.recs = (qa::PixRec*)(ws + off_recs);
-  a.flag_list = (int*)(ws + off_list);
-  a.tie_list = (qa::TieEntry*)(ws + off_tie);
+  a.one.md = m->d_md;
+  a.one.n = m->n;
+  a.one.ng = m->ng;
+  a.one.sc = sc;
+  a.one.mt.t = t;
+  a.one.mt.closed = closed ? 1 : 0;
+  a.one.mt.n_charges = closed ? n_charges : 0;
+  a.one.mt.carrier = m->carrier;
+  a.one.cfg = choose_cfg(m->n, t, P, m->num_sms);
+  a.one.klass = qa::search_klass(a.one.cfg);
+  a.one.prep_team = prep_team(m->n);
+  a.one.rk = raster_constants(m, sc);
+  a.one.bx_analytic = 4.0e-7f;
+  a.one.bx_qp_scale = 0.f;  // derived from the device model's condition number
+  a.one.recs = (qa::PixRec*)(ws + off_recs);
+  a.flag_list = (qa::ListEntry*)(ws + off_list);
+  a.tie_list = (qa::ListEntry*)(ws + off_tie);
   a.bc_prep = m->d_bc_prep;
   a.bc_search = m->d_bc_search;
   a.cnt = m->d_cnt;
-  a.out_n = out_n;
-  a.out_U = out_U;
-  a.out_flags = out_flags;
+  a.one.out_n = out_n;
+  a.one.out_U = out_U;
+  a.one.out_flags = out_flags;
   a.num_sms = m->num_sms;
-  m->last_cfg = a.cfg;
+  m->last_cfg = a.one.cfg;
   m->last_P = P;
   a.ev = m->timing ? m->ev : nullptr;
   m->last_kind = 1;
@@ -409,7 +411,7 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
   else if (m->n <= 8) cfg = {5, 4, 8};
   else cfg = {5, 4, 32};
   const size_t off_list = align_up(sizeof(qa::Counters), 256);
-  const size_t off_bcp = align_up(off_list + sizeof(int) * (size_t)P, 256);
+  const size_t off_bcp = align_up(off_list + sizeof(qa::ListEntry) * (size_t)P, 256);
   const size_t off_recs = align_up(off_bcp + sizeof(qa::BlockCounts) * ((size_t)P + 1), 256);
   const size_t off_part = align_up(off_recs + sizeof(qa::PixRec) * (size_t)P, 256);
   const size_t total =
@@ -423,20 +425,21 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
 
   qa::GsLaunch g;
   std::memset(&g, 0, sizeof(g));
-  g.md = m->d_md;
-  g.n = m->n;
-  g.ng = m->ng;
-  g.sc = sc;
-  g.mt.t = t;
-  g.mt.closed = closed ? 1 : 0;
-  g.mt.n_charges = closed ? n_charges : 0;
-  g.mt.carrier = m->carrier;
-  g.cfg = cfg;
-  g.prep_team = prep_team(m->n);
-  g.rk = raster_constants(m, sc);
-  g.bx_analytic = 4.0e-7f;
-  g.recs = (qa::PixRec*)(ws + off_recs);
-  g.flag_list = (int*)(ws + off_list);
+  g.one.md = m->d_md;
+  g.one.n = m->n;
+  g.one.ng = m->ng;
+  g.one.sc = sc;
+  g.one.mt.t = t;
+  g.one.mt.closed = closed ? 1 : 0;
+  g.one.mt.n_charges = closed ? n_charges : 0;
+  g.one.mt.carrier = m->carrier;
+  g.one.cfg = cfg;
+  g.one.klass = qa::search_klass(cfg);
+  g.one.prep_team = prep_team(m->n);
+  g.one.rk = raster_constants(m, sc);
+  g.one.bx_analytic = 4.0e-7f;
+  g.one.recs = (qa::PixRec*)(ws + off_recs);
+  g.flag_list = (qa::ListEntry*)(ws + off_list);
   g.bc_prep = m->d_bc_prep;
   g.cnt = m->d_cnt;
   g.num_sms = m->num_sms;
@@ -451,10 +454,10 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
   a.n = m->n;
   a.ng = m->ng;
   a.sc = sc;
-  a.mt = g.mt;
+  a.mt = g.one.mt;
   a.cfg = cfg;
   a.kT = kT;
-  a.recs = g.recs;
+  a.recs = g.one.recs;
   a.cnt = m->d_cnt;
   a.out_mean = out_mean;
   a.out_logZ = out_logZ;
@@ -715,8 +718,8 @@ namespace {
 constexpr size_t kStaticPixels = (size_t)QA_STATIC_MAX_PIXELS;
 constexpr size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 constexpr size_t kStOffList = al256(sizeof(qa::Counters));
-constexpr size_t kStOffTie = al256(kStOffList + sizeof(int) * kStaticPixels);
-constexpr size_t kStOffBcp = al256(kStOffTie + sizeof(qa::TieEntry) * kStaticPixels);
+constexpr size_t kStOffTie = al256(kStOffList + sizeof(qa::ListEntry) * kStaticPixels);
+constexpr size_t kStOffBcp = al256(kStOffTie + sizeof(qa::ListEntry) * kStaticPixels);
 constexpr size_t kStOffBcs = al256(kStOffBcp + sizeof(qa::BlockCounts) * (kStaticPixels + 1));
 constexpr size_t kStOffRecs = al256(kStOffBcs + sizeof(qa::BlockCounts) * (kStaticPixels + 1));
 constexpr size_t kStaticBytes = al256(kStOffRecs + sizeof(qa::PixRec) * kStaticPixels);
@@ -781,31 +784,247 @@ extern "C" int qa_ground_state_open_static(qa_model* m, const qa_raster* r,
 
   qa::GsLaunch a;
   std::memset(&a, 0, sizeof(a));
-  a.md = m->d_md;
-  a.n = m->n;
-  a.ng = m->ng;
-  a.sc = sc;
-  a.mt.t = threshold;
-  a.mt.closed = 0;
-  a.mt.n_charges = 0;
-  a.mt.carrier = m->carrier;
-  a.cfg = choose_cfg(m->n, threshold, P, m->num_sms);
-  a.prep_team = prep_team(m->n);
-  a.rk = raster_constants(m, sc);
-  a.bx_analytic = 4.0e-7f;
-  a.bx_qp_scale = 0.f;
-  a.recs = (qa::PixRec*)(ws + kStOffRecs);
-  a.flag_list = (int*)(ws + kStOffList);
-  a.tie_list = (qa::TieEntry*)(ws + kStOffTie);
+  a.one.md = m->d_md;
+  a.one.n = m->n;
+  a.one.ng = m->ng;
+  a.one.sc = sc;
+  a.one.mt.t = threshold;
+  a.one.mt.closed = 0;
+  a.one.mt.n_charges = 0;
+  a.one.mt.carrier = m->carrier;
+  a.one.cfg = choose_cfg(m->n, threshold, P, m->num_sms);
+  a.one.klass = qa::search_klass(a.one.cfg);
+  a.one.prep_team = prep_team(m->n);
+  a.one.rk = raster_constants(m, sc);
+  a.one.bx_analytic = 4.0e-7f;
+  a.one.bx_qp_scale = 0.f;
+  a.one.recs = (qa::PixRec*)(ws + kStOffRecs);
+  a.flag_list = (qa::ListEntry*)(ws + kStOffList);
+  a.tie_list = (qa::ListEntry*)(ws + kStOffTie);
   a.bc_prep = (qa::BlockCounts*)(ws + kStOffBcp);
   a.bc_search = (qa::BlockCounts*)(ws + kStOffBcs);
   a.cnt = cnt;
-  a.out_n = out_n;
-  a.out_U = out_U;
-  a.out_flags = out_flags;
+  a.one.out_n = out_n;
+  a.one.out_U = out_U;
+  a.one.out_flags = out_flags;
   a.num_sms = m->num_sms;
   a.ev = nullptr;
   e = qa::launch_ground_state(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "ground-state launch");
   return QA_OK;
 }
+
+// ---------------------------------------------------------------------------
+// batched ground state
+// ---------------------------------------------------------------------------
+struct qa_batch {
+  int device = 0, num_sms = 0, count = 0;
+  long long pixels = 0;
+  qa::GsLaunch L;
+  void* mem = nullptr;  // one allocation: table, units, scratch
+  std::vector<long long> P;
+  std::vector<qa::SearchCfg> cfg;
+};
+
+namespace {
+
+// Estimated candidate evaluations per pixel of an array (for unit sizing and
+// the largest-first order).
+double unit_cost(const qa::ArrayDesc& d) {
+  const double kexp = d.mt.t >= 1.0 ? d.n : d.n * std::log2(1.0 + d.mt.t);
+  return std::pow(2.0, kexp) + 64.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qa_batch_create(const qa_batch_item* items, int count, qa_batch** out) {
+  if (!out) return fail(QA_ERR_INVALID, "null out");
+  *out = nullptr;
+  if (!items || count < 1) return fail(QA_ERR_SHAPE, "empty batch");
+  qa_batch* b = new qa_batch();
+  std::vector<qa::ArrayDesc> table((size_t)count);
+  int rc = QA_OK;
+  for (int i = 0; i < count && rc == QA_OK; ++i) {
+    const qa_batch_item& it = items[i];
+    qa_model* m = it.model;
+    if (!m) { rc = fail(QA_ERR_INVALID, "item %d: null model", i); break; }
+    if (i == 0) { b->device = m->device; b->num_sms = m->num_sms; }
+    if (m->device != b->device) { rc = fail(QA_ERR_SHAPE, "item %d: models on different devices", i); break; }
+    if (!(it.threshold >= 0.0 && it.threshold <= 1.0)) { rc = fail(QA_ERR_RANGE, "item %d: threshold %g", i, it.threshold); break; }
+    if (it.closed && (it.n_charges < 0 || it.n_charges > 100000)) { rc = fail(QA_ERR_RANGE, "item %d: n_charges %d", i, it.n_charges); break; }
+    if (it.team != 0 && (it.team < 1 || it.team > 32 || (it.team & (it.team - 1)))) { rc = fail(QA_ERR_RANGE, "item %d: team %d", i, it.team); break; }
+    ScanIn in;
+    in.r = &it.raster;
+    qa::Scan sc;
+    if ((rc = make_scan(m, in, &sc))) break;
+    if (!it.out_n) { rc = fail(QA_ERR_INVALID, "item %d: null out_n", i); break; }
+    qa::ArrayDesc& d = table[(size_t)i];
+    std::memset(&d, 0, sizeof(d));
+    d.md = m->d_md;
+    d.n = m->n;
+    d.ng = m->ng;
+    d.sc = sc;
+    d.rk = raster_constants(m, sc);
+    d.mt.t = it.threshold;
+    d.mt.closed = it.closed ? 1 : 0;
+    d.mt.n_charges = it.closed ? it.n_charges : 0;
+    d.mt.carrier = m->carrier;
+    d.cfg = choose_cfg(m->n, it.threshold, 1LL << 40, m->num_sms);  // no small-raster spreading
+    if (it.team) d.cfg.T = it.team;
+    d.klass = qa::search_klass(d.cfg);
+    d.prep_team = prep_team(m->n);
+    d.bx_analytic = 4.0e-7f;
+    d.bx_qp_scale = 0.f;
+    d.out_n = it.out_n;
+    d.out_U = it.out_U;
+    d.out_flags = it.out_flags;
+    b->P.push_back(sc.P);
+    b->cfg.push_back(d.cfg);
+    b->pixels += sc.P;
+  }
+  if (rc) { delete b; return rc; }
+  b->count = count;
+  // work units: prep in runs of ~4096 pixels; search in runs worth about
+  // 2^18 candidate evaluations, largest first
+  std::vector<qa::WorkUnit> pu, su;
+  std::vector<double> scost;
+  for (int i = 0; i < count; ++i) {
+    const qa::ArrayDesc& d = table[(size_t)i];
+    const long long P = b->P[(size_t)i];
+    const long long tpb = 128 / d.prep_team;
+    const long long pchunk = std::max(tpb, (4096 / tpb) * tpb);
+    for (long long f = 0; f < P; f += pchunk)
+      pu.push_back({i, (int)std::min(pchunk, P - f), f});
+    const long long teams = 128 / d.cfg.T;
+    const double c = unit_cost(d);
+    long long k = (long long)std::max(1.0, std::floor(262144.0 / (c * (double)teams)));
+    k = std::min(k, 64LL);
+    const long long schunk = teams * k;
+    for (long long f = 0; f < P; f += schunk) {
+      const long long cnt = std::min(schunk, P - f);
+      su.push_back({i, (int)cnt, f});
+      scost.push_back(c * (double)cnt);
+    }
+  }
+  std::vector<size_t> order(su.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](size_t x, size_t y) { return scost[x] > scost[y]; });
+  std::vector<qa::WorkUnit> su_sorted(su.size());
+  for (size_t i = 0; i < order.size(); ++i) su_sorted[i] = su[order[i]];
+
+  if ((rc = select_device(items[0].model))) { delete b; return rc; }
+  int pps = 1, sps = 1;
+  qa::batch_occupancy(&pps, &sps);
+  const int grid_prep = b->num_sms * pps, grid_search = b->num_sms * sps;
+  const size_t Ptot = (size_t)std::max(1LL, b->pixels);
+  const size_t off_cnt = 0;
+  const size_t off_tab = align_up(sizeof(qa::Counters), 256);
+  const size_t off_pu = align_up(off_tab + sizeof(qa::ArrayDesc) * (size_t)count, 256);
+  const size_t off_su = align_up(off_pu + sizeof(qa::WorkUnit) * pu.size(), 256);
+  const size_t off_fl = align_up(off_su + sizeof(qa::WorkUnit) * su_sorted.size(), 256);
+  const size_t off_tl = align_up(off_fl + sizeof(qa::ListEntry) * Ptot, 256);
+  const size_t off_bcp = align_up(off_tl + sizeof(qa::ListEntry) * Ptot, 256);
+  const size_t off_bcs = align_up(off_bcp + sizeof(qa::BlockCounts) * (size_t)grid_prep, 256);
+  const size_t off_rec = align_up(off_bcs + sizeof(qa::BlockCounts) * (size_t)grid_search, 256);
+  const size_t total = off_rec + sizeof(qa::PixRec) * Ptot;
+  cudaError_t e = cudaMalloc(&b->mem, total);
+  if (e != cudaSuccess) {
+    delete b;
+    return fail(QA_ERR_NOMEM, "batch scratch of %zu bytes: %s", total, cudaGetErrorString(e));
+  }
+  char* mem = (char*)b->mem;
+  long long roff = 0;
+  for (int i = 0; i < count; ++i) {
+    table[(size_t)i].recs = (qa::PixRec*)(mem + off_rec) + roff;
+    roff += b->P[(size_t)i];
+  }
+  e = cudaMemcpy(mem + off_tab, table.data(), sizeof(qa::ArrayDesc) * (size_t)count,
+                 cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !pu.empty())
+    e = cudaMemcpy(mem + off_pu, pu.data(), sizeof(qa::WorkUnit) * pu.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !su_sorted.empty())
+    e = cudaMemcpy(mem + off_su, su_sorted.data(), sizeof(qa::WorkUnit) * su_sorted.size(),
+                   cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(b->mem);
+    delete b;
+    return cuda_fail(e, "batch upload");
+  }
+  qa::GsLaunch& L = b->L;
+  std::memset(&L, 0, sizeof(L));
+  L.table = (const qa::ArrayDesc*)(mem + off_tab);
+  L.prep_units = (const qa::WorkUnit*)(mem + off_pu);
+  L.n_prep_units = (int)pu.size();
+  L.search_units = (const qa::WorkUnit*)(mem + off_su);
+  L.n_search_units = (int)su_sorted.size();
+  L.flag_list = (qa::ListEntry*)(mem + off_fl);
+  L.tie_list = (qa::ListEntry*)(mem + off_tl);
+  L.cnt = (qa::Counters*)(mem + off_cnt);
+  L.bc_prep = (qa::BlockCounts*)(mem + off_bcp);
+  L.bc_search = (qa::BlockCounts*)(mem + off_bcs);
+  L.grid_prep = grid_prep;
+  L.grid_search = grid_search;
+  L.num_sms = b->num_sms;
+  L.ev = nullptr;
+  *out = b;
+  return QA_OK;
+}
+
+int qa_batch_run(qa_batch* b, void* stream) {
+  if (!b) return fail(QA_ERR_INVALID, "null batch");
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e == cudaSuccess && cur != b->device) e = cudaSetDevice(b->device);
+  if (e != cudaSuccess) return cuda_fail(e, "device");
+  e = qa::launch_ground_state_batch(b->L, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+  return QA_OK;
+}
+
+int qa_batch_stats(qa_batch* b, void* stream, qa_stats* out) {
+  if (!b || !out) return fail(QA_ERR_INVALID, "null argument");
+  std::memset(out, 0, sizeof(*out));
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  qa::Counters c;
+  if (e == cudaSuccess) e = cudaMemcpy(&c, b->L.cnt, sizeof(c), cudaMemcpyDeviceToHost);
+  std::vector<qa::BlockCounts> bp((size_t)b->L.grid_prep), bs((size_t)b->L.grid_search);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(bp.data(), b->L.bc_prep, sizeof(qa::BlockCounts) * bp.size(), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(bs.data(), b->L.bc_search, sizeof(qa::BlockCounts) * bs.size(), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "batch counters read");
+  for (const auto& x : bp) { c.candidates += x.candidates; c.qp += x.qp; c.doubled += x.doubled; }
+  for (const auto& x : bs) {
+    c.evaluated += x.evaluated;
+    c.near_tie += x.near_tie;
+    c.boundary += x.boundary;
+    c.overflow += x.overflow;
+  }
+  out->pixels = b->pixels;
+  out->candidates = (long long)c.candidates;
+  out->evaluated = (long long)c.evaluated;
+  out->qp_pixels = (long long)c.qp;
+  out->near_tie = (long long)c.near_tie;
+  out->boundary = (long long)c.boundary;
+  out->flagged = out->near_tie + out->boundary;
+  out->unresolved = (long long)c.unresolved;
+  out->overflow = (long long)c.overflow;
+  out->doubled = (long long)c.doubled;
+  out->shortlist_max = (long long)c.shortlist_max;
+  out->resolved = (long long)c.resolved;
+  return QA_OK;
+}
+
+int qa_batch_destroy(qa_batch* b) {
+  if (!b) return QA_OK;
+  cudaSetDevice(b->device);
+  cudaDeviceSynchronize();
+  if (b->mem) cudaFree(b->mem);
+  delete b;
+  return QA_OK;
+}
+
+}  // extern "C"

@@ -147,12 +147,17 @@ struct Counters {
       unresolved, overflow, doubled, shortlist_max, resolved;
   unsigned int n_flag;  // length of the FP64 recheck list
   unsigned int n_tie;   // length of the near-tie list
+  unsigned int q_prep;  // batched launch: work-queue heads
+  unsigned int q_search;
 };
 
-// A near-tie pixel and the FP32 minimum its search found.
-struct TieEntry {
+// A pixel queued for the near-tie resolve or the FP64 recheck: its array (0
+// for a single-array call), its index and the FP32 minimum of its search.
+struct ListEntry {
+  int array;
   int p;
   float m1;
+  int pad;
 };
 
 // Copy the model's FP32 constants into shared memory (16-byte vectors).

@@ -1,0 +1,751 @@
+// qa_gs_tiles.cuh -- the ground-state stages as per-tile device functions,
+// shared by the single-array kernels (qa_kernels_gs.cu) and the persistent
+// batched kernels (qa_batch.cu).  A tile is one block's worth of pixels of one
+// array; the stage functions take the array's descriptor and the tile's first
+// pixel-team index, so both launch shapes run exactly the same code.
+#pragma once
+
+#include "qa_launch.h"
+#include "qa_prep.cuh"
+#include "qa_search.cuh"
+
+namespace qa {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPrepThreads = 128;
+constexpr int kSearchThreads = 128;
+constexpr int kRecheckThreads = 128;
+constexpr int kResolveThreads = 256;
+constexpr int kCheckL1 = 4, kCheckL2 = 3;  // resolve/recheck split: 2^9 outer states at k = 16
+constexpr unsigned kBcap = 1024;
+
+// number of k-subsets of size w (k <= 16)
+__device__ __forceinline__ unsigned long long binom(int k, int w) {
+  if (w < 0 || w > k) return 0ull;
+  unsigned long long r = 1ull;
+  for (int i = 1; i <= w; ++i) r = r * (unsigned long long)(k - w + i) / (unsigned long long)i;
+  return r;
+}
+
+// The descriptor of a list entry's array.
+__device__ __forceinline__ const ArrayDesc& desc_of(const GsLaunch& L, int array) {
+  return L.table ? L.table[array] : L.one;
+}
+
+// ---------------------------------------------------------------------------
+// (a0) raster constants of a block: c(ix, iy) = c0 + ix du + iy dw with
+// c0 = s Cgd (V0 + x0 u + y0 w), du = s Cgd u dx, dw = s Cgd w dy, formed in
+// double-float FP32 from FP64 inputs (one FP64 rounding per input, no FP64
+// dependency chains: FP64 issues at a small fraction of the FP32 rate here).
+// Used when the host could not precompute them (model updated on the GPU).
+// ---------------------------------------------------------------------------
+__device__ inline void raster_consts(const ModelData* md, int n, int ng, const Scan& sc,
+                                     double carrier, df* sV, df* sU, df* sW, df* c0,
+                                     df* du, df* dw) {
+  for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+    sV[g] = df_from_double(sc.V0[g] + sc.x0 * sc.u[g] + sc.y0 * sc.w[g]);
+    sU[g] = df_from_double(sc.u[g] * sc.dx);
+    sW[g] = df_from_double(sc.w[g] * sc.dy);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 3 * n; e += blockDim.x) {
+    const int i = e % n, which = e / n;
+    const df* vec = which == 0 ? sV : (which == 1 ? sU : sW);
+    df acc = {0.f, 0.f};
+    for (int g = 0; g < ng; ++g)
+      acc = df_add(acc, df_mul(df_from_double(carrier * md->Cgd[i * ng + g]), vec[g]));
+    (which == 0 ? c0 : (which == 1 ? du : dw))[i] = acc;
+  }
+}
+
+// Block sum of per-thread counts (all threads must call; result in thread 0).
+template <typename U>
+__device__ __forceinline__ U block_sum(U v, U* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  U t = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// prep stage: shared state of a block and the per-array set-up
+// ---------------------------------------------------------------------------
+struct PrepShared {
+  ModelConsts cs;
+  df sV[kMaxGate], sU[kMaxGate], sW[kMaxGate];
+  df sc0[kMaxDot], sdu[kMaxDot], sdw[kMaxDot];
+  float sx[kPrepThreads];
+  int sst[kPrepThreads];
+  unsigned long long red64[kPrepThreads / 32];
+  unsigned red32[kPrepThreads / 32];
+};
+
+// Stage an array's FP32 model constants and raster constants (all threads).
+__device__ inline void prep_stage_array(const ArrayDesc& a, PrepShared& sh) {
+  stage_consts(&a.md->k, &sh.cs);
+  if (a.sc.kind == 0) {
+    if (a.rk.valid) {
+      if (threadIdx.x < kMaxDot) {
+        sh.sc0[threadIdx.x] = a.rk.c0[threadIdx.x];
+        sh.sdu[threadIdx.x] = a.rk.du[threadIdx.x];
+        sh.sdw[threadIdx.x] = a.rk.dw[threadIdx.x];
+      }
+    } else {
+      raster_consts(a.md, a.n, a.ng, a.sc, a.mt.carrier, sh.sV, sh.sU, sh.sW, sh.sc0,
+                    sh.sdu, sh.sdw);
+    }
+  }
+  __syncthreads();
+}
+
+// Per-block totals of the prep stage (thread 0's copy is the block's).
+struct PrepAcc {
+  unsigned long long candidates = 0;
+  unsigned qp = 0, doubled = 0;
+};
+
+// ---------------------------------------------------------------------------
+// (a1)-(a4) for one tile: induced charge, continuous minimum, candidate set,
+// h = M (base - c).  A team of TP lanes (a power of two >= N, at most 16)
+// prepares one pixel, lane i owning dot i; team-wide sums, ballots and gathers
+// use shuffles restricted to the team's lanes, so teams of one warp may
+// diverge.  Pixels team_base + threadIdx.x / TP below p_end are processed.
+// All threads of the block must call (block reductions at the end).
+// ---------------------------------------------------------------------------
+template <bool CLOSED>
+__device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long team_base,
+                                 long long p_end, PrepAcc& tot) {
+  const int n = a.n;
+  const float* sMhi = sh.cs.Mhi;
+  const float* sMlo = sh.cs.Mlo;
+  const float bx_qp_scale = a.bx_qp_scale > 0.f ? a.bx_qp_scale : sh.cs.bx_qp_scale;
+  const bool model_bad = sh.cs.model_bad != 0;
+
+  const int TP = a.prep_team;
+  const int lt = threadIdx.x & (TP - 1);
+  const int lane = threadIdx.x & 31;
+  const int tbase = lane & ~(TP - 1);                   // team's first lane
+  const unsigned tmask = (TP == 32 ? 0xffffffffu : ((1u << TP) - 1u)) << tbase;
+  const long long p = team_base + threadIdx.x / TP;
+  const bool active = p < p_end;
+  const bool live = active && lt < n;
+  const int nhat = a.mt.n_charges;
+
+  // team reductions over lanes (dead lanes contribute zero)
+  auto tsum_f = [&](float v) {
+    for (int off = 1; off < TP; off <<= 1) v += __shfl_xor_sync(tmask, v, off, TP);
+    return v;
+  };
+  auto tmax_f = [&](float v) {
+    for (int off = 1; off < TP; off <<= 1) v = fmaxf(v, __shfl_xor_sync(tmask, v, off, TP));
+    return v;
+  };
+  auto tsum_i = [&](int v) {
+    for (int off = 1; off < TP; off <<= 1) v += __shfl_xor_sync(tmask, v, off, TP);
+    return v;
+  };
+  auto tsum_df = [&](df v) {
+    for (int off = 1; off < TP; off <<= 1) {
+      df o;
+      o.hi = __shfl_xor_sync(tmask, v.hi, off, TP);
+      o.lo = __shfl_xor_sync(tmask, v.lo, off, TP);
+      v = df_add(v, o);
+    }
+    return v;
+  };
+  auto tballot = [&](bool pred) { return (__ballot_sync(tmask, pred) & tmask) >> tbase; };
+
+  // (a1) c_i
+  df c = {0.f, 0.f};
+  if (live) {
+    if (a.sc.kind == 0) {
+      const int ix = (int)(p % a.sc.W), iy = (int)(p / a.sc.W);
+      c = raster_c(sh.sc0[lt], sh.sdu[lt], sh.sdw[lt], ix, iy);
+    } else {
+      c = point_c(&a.md->Cgd[lt * a.ng], &a.sc.V[p * a.ng], a.ng, a.mt.carrier);
+    }
+  }
+  // (a2) analytic continuous minimum (Appendix C / D)
+  df x = c;
+  if (CLOSED) {
+    const df csum = tsum_df(c);
+    const df lam = df_sub({(float)nhat, 0.f}, csum);  // N_hat <= 2^24
+    if (live) x = df_add(c, df_mul(lam, sh.cs.vs[lt]));
+  }
+  const unsigned A =
+      tballot(live && (x.hi < 0.f || (x.hi == 0.f && x.lo < 0.f)));
+  unsigned flags = 0u;
+  float bx = a.bx_analytic;
+  const float cmax = tmax_f(live ? fabsf(c.hi + c.lo) : 0.f);
+  if (A) {  // (a3) QP, solved by the team's first lane
+    flags |= kFlagQP;
+    if (CLOSED && nhat == 0) {
+      x = {0.f, 0.f};
+    } else {
+      const float scale = 1.f + cmax + (float)nhat;
+      bx = fmaxf(bx, bx_qp_scale * scale);
+      sh.sx[threadIdx.x] = c.hi + c.lo;
+      __syncwarp(tmask);
+      if (lt == 0) {
+        float cf[kMaxDot], xf[kMaxDot];
+        for (int j = 0; j < n; ++j) cf[j] = sh.sx[threadIdx.x + j];
+        const int st = qp_active_set<float>(n, sh.cs.Cdd, kLdM, cf, CLOSED, (float)nhat,
+                                            sh.cs.sv, sh.cs.s_s, A, 0.25f * bx_qp_scale * scale,
+                                            4 * n + 4, xf);
+        for (int j = 0; j < n; ++j) sh.sx[threadIdx.x + j] = xf[j];
+        sh.sst[threadIdx.x] = st;
+      }
+      __syncwarp(tmask);
+      if (live) x = {sh.sx[threadIdx.x], 0.f};
+      if (sh.sst[threadIdx.x - lt] != 0) flags |= kFlagQPCap;
+      __syncwarp(tmask);
+    }
+  }
+
+  // (a4) candidate set; the closed doubling loop is team-uniform
+  double tt = a.mt.t;
+  unsigned mask = 0u;
+  int w = -1, base = 0;
+  bool amb = false;
+  for (int iter = 0; iter < 40; ++iter) {
+    const float th = __double2float_rn(0.5 * tt);
+    bool bnd = false;
+    if (live) {
+      df xi = x;
+      if (xi.hi < 0.f || (xi.hi == 0.f && xi.lo < 0.f)) xi = {0.f, 0.f};
+      float fl = floorf(xi.hi);
+      if (xi.hi == fl && xi.lo < 0.f) fl -= 1.f;
+      const float fr = __fadd_rn(__fsub_rn(xi.hi, fl), xi.lo);
+      amb = fabsf(fr - 0.5f) <= th;
+      base = (int)fl + ((!amb && fr >= 0.5f) ? 1 : 0);
+      bnd = (xi.hi >= 0.5f - bx && fminf(fr, 1.f - fr) < bx) ||
+            (tt < 1.0 && fabsf(fabsf(fr - 0.5f) - th) < bx);
+    }
+    if (tballot(bnd)) flags |= kFlagBoundary;
+    mask = tballot(live && amb);
+    const int sum = tsum_i(live ? base : 0);
+    if (!CLOSED) break;
+    w = nhat - sum;
+    if (w >= 0 && w <= __popc(mask)) break;
+    if (tt >= 1.0) {  // impossible in exact arithmetic: settle in FP64
+      flags |= kFlagBoundary;
+      w = w < 0 ? 0 : __popc(mask);
+      break;
+    }
+    tt = (tt <= 0.0) ? 1.0 : fmin(2.0 * tt, 1.0);
+    flags |= kFlagDoubled;
+  }
+  if (model_bad) flags |= kFlagUnresolved;
+
+  // h_i = (M (base - c))_i in double-float, r_j gathered from the team
+  const df r = df_sub({(float)base, 0.f}, c);
+  df acc = {0.f, 0.f};
+  for (int j = 0; j < n; ++j) {
+    df rj;
+    rj.hi = __shfl_sync(tmask, r.hi, j, TP);
+    rj.lo = __shfl_sync(tmask, r.lo, j, TP);
+    if (live) acc = df_add(acc, df_mul({sMhi[lt * kLdM + j], sMlo[lt * kLdM + j]}, rj));
+  }
+  const float h = acc.hi + acc.lo;
+  float Si = 0.f;
+  if (live && amb) {
+    Si = fabsf(h) + 0.5f * sMhi[lt * kLdM + lt];
+    for (unsigned m2 = mask & ((1u << lt) - 1u); m2; m2 &= m2 - 1u)
+      Si += fabsf(sMhi[lt * kLdM + (__ffs(m2) - 1)]);
+  }
+  const float S = tsum_f(Si);
+  const int k = __popc(mask);
+
+  PixRec* rec = a.recs + (active ? p : 0);
+  if (live) {
+    rec->h[lt] = h;
+    rec->chi[lt] = c.hi;
+    rec->clo[lt] = c.lo;
+    rec->base[lt] = (short)base;
+  }
+  unsigned long long my_cand = 0;
+  unsigned my_qp = 0, my_doubled = 0;
+  if (active && lt == 0) {
+    rec->mask = (unsigned short)mask;
+    rec->k = (unsigned char)k;
+    rec->w = (signed char)(CLOSED ? w : -1);
+    rec->flags = (unsigned char)flags;
+    rec->bound = near_tie_bound(S, k, a.cfg.L2);
+    my_cand = CLOSED ? binom(k, w) : (1ull << k);
+    my_qp = (flags & kFlagQP) ? 1u : 0u;
+    my_doubled = (flags & kFlagDoubled) ? 1u : 0u;
+  }
+  __syncwarp();
+  const unsigned long long bc = block_sum(my_cand, sh.red64);
+  const unsigned bq = block_sum(my_qp, sh.red32);
+  const unsigned bd = block_sum(my_doubled, sh.red32);
+  if (threadIdx.x == 0) {
+    tot.candidates += bc;
+    tot.qp += bq;
+    tot.doubled += bd;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// search stage: shared state of a block
+// ---------------------------------------------------------------------------
+struct SearchShared {
+  ModelConsts cs;
+  int sdot[kSearchThreads][kMaxDot];
+  float sh[kSearchThreads][kMaxDot];
+  unsigned long long red64[kSearchThreads / 32];
+  unsigned red32[kSearchThreads / 32];
+};
+
+struct SearchAcc {
+  unsigned long long evaluated = 0;
+  unsigned near_tie = 0, boundary = 0, overflow = 0;
+};
+
+// ---------------------------------------------------------------------------
+// (a5)-(a6), (a8) for one tile: candidate search, top-two selection, outputs.
+// A team of T lanes (the array's cfg.T) searches one pixel; pixels
+// team_base + threadIdx.x / T below p_end.  Pixels whose candidate set is in
+// doubt go on the FP64 recheck list, near ties on the resolve list.  All
+// threads of the block must call.
+// ---------------------------------------------------------------------------
+template <int L1, int L2, bool CLOSED>
+__device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, SearchShared& sh,
+                                   int array, long long team_base, long long p_end,
+                                   SearchAcc& acc) {
+  const int n = a.n;
+  const float* sM = sh.cs.Mhi;
+  const float* sMlo = sh.cs.Mlo;
+
+  const int T = a.cfg.T;
+  const int team = threadIdx.x / T, lt = threadIdx.x % T;
+  const long long p = team_base + team;
+  const bool active = p < p_end;
+  const PixRec* rec = a.recs + (active ? p : 0);
+  const unsigned mask = active ? rec->mask : 0u;
+  const int k = __popc(mask);
+  if (active && lt == 0) {
+    int s = 0;
+    for (unsigned m = mask; m; m &= m - 1u) {
+      const int i = __ffs(m) - 1;
+      sh.sdot[team][s] = i;
+      sh.sh[team][s] = rec->h[i];
+      ++s;
+    }
+  }
+  __syncwarp();
+  float m1 = kInf, m2 = kInf;
+  unsigned b1 = 0u;
+  unsigned long long ev = 0;
+  if (active) {
+    SlotView sv{sh.sdot[team], sh.sh[team], k, (int)rec->w};
+    search_lane<L1, L2, CLOSED, false>(sM, sv, lt, T, 0.f, nullptr, nullptr, 0u,
+                                       m1, b1, m2, ev);
+  }
+  for (int off = 1; off < T; off <<= 1) {
+    const float om1 = __shfl_xor_sync(kFull, m1, off);
+    const unsigned ob1 = __shfl_xor_sync(kFull, b1, off);
+    const float om2 = __shfl_xor_sync(kFull, m2, off);
+    top2_merge(m1, b1, m2, om1, ob1, om2);
+  }
+
+  // epilogue: n* = base + bits, U(n*) = 1/2 r^T M r in double-float (team
+  // lanes split the rows; no per-thread arrays, so nothing lands in local
+  // memory)
+  df u = {0.f, 0.f};
+  unsigned flags = 0u;
+  if (active) {
+    for (int i = lt; i < n; i += T) {
+      df acc = {0.f, 0.f};
+      for (int j = 0; j < n; ++j) {
+        int nj = rec->base[j];
+        if ((mask >> j) & 1u) nj += (int)((b1 >> __popc(mask & ((1u << j) - 1u))) & 1u);
+        const df rj = df_sub({(float)nj, 0.f}, {rec->chi[j], rec->clo[j]});
+        acc = df_add(acc, df_mul({sM[i * kLdM + j], sMlo[i * kLdM + j]}, rj));
+      }
+      int ni = rec->base[i];
+      if ((mask >> i) & 1u) ni += (int)((b1 >> __popc(mask & ((1u << i) - 1u))) & 1u);
+      const df ri = df_sub({(float)ni, 0.f}, {rec->chi[i], rec->clo[i]});
+      u = df_add(u, df_mul(acc, ri));
+      if (ni > 127) { ni = 127; flags |= kFlagOverflow; }
+      a.out_n[p * n + i] = (int8_t)ni;
+    }
+  }
+  for (int off = 1; off < T; off <<= 1) {
+    df o;
+    o.hi = __shfl_xor_sync(kFull, u.hi, off);
+    o.lo = __shfl_xor_sync(kFull, u.lo, off);
+    u = df_add(u, o);
+    flags |= __shfl_xor_sync(kFull, flags, off);
+  }
+  unsigned my_nt = 0, my_bd = 0, my_ov = 0;
+  if (active) {
+    flags |= rec->flags;
+    if (!(m2 - m1 > rec->bound)) flags |= kFlagNearTie;
+    if (lt == 0) {
+      if (a.out_U) a.out_U[p] = 0.5 * df_to_double(u);
+      if (flags & (kFlagBoundary | kFlagQPCap | kFlagUnresolved)) {
+        // the candidate set itself may be wrong: FP64 recheck
+        const unsigned at = atomicAdd(&L.cnt->n_flag, 1u);
+        L.flag_list[at] = ListEntry{array, (int)p, m1, 0};
+        my_bd = 1;
+      } else if (flags & kFlagNearTie) {
+        // right set, uncertain order: exact energies of the close candidates
+        const unsigned at = atomicAdd(&L.cnt->n_tie, 1u);
+        L.tie_list[at] = ListEntry{array, (int)p, m1, 0};
+        my_nt = 1;
+      }
+      my_ov = (flags & kFlagOverflow) ? 1u : 0u;
+      if (a.out_flags) a.out_flags[p] = (uint8_t)flags;
+    }
+  }
+  const unsigned long long bev = block_sum(ev, sh.red64);
+  const unsigned bnt = block_sum(my_nt, sh.red32);
+  const unsigned bbd = block_sum(my_bd, sh.red32);
+  const unsigned bov = block_sum(my_ov, sh.red32);
+  if (threadIdx.x == 0) {
+    acc.evaluated += bev;
+    acc.near_tie += bnt;
+    acc.boundary += bbd;
+    acc.overflow += bov;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// (a7, near ties) for one list entry: a pixel whose candidate set is certain
+// but whose FP32 best/runner-up gap is under the error bound.  The block
+// re-walks the candidates collecting every block of the split whose FP32
+// minimum is within the bound of the search's minimum (the exact argmin is
+// guaranteed to be among them) and evaluates those candidates exactly,
+// relative to the base state,
+//     E(b) = sum_{s in b} (h_s + M_ss / 2) + sum_{s < s' in b} M_ss',
+// in double-float arithmetic with h = M (base - c) in double-float (about
+// 1e-13 absolute).  No FP64 instructions: GB300's FP64 rate is a small
+// fraction of its FP32 rate.  A pixel whose two best exact energies are
+// within 1e-10 (a true tie) or whose list overflows goes on to the FP64
+// recheck, which also applies the lexicographic tie rule.  The resolve split
+// is kCheckL1 / kCheckL2 for every array; the search's bound covers it (it
+// was derived for a middle level at least as deep).
+// ---------------------------------------------------------------------------
+struct ResolveShared {
+  ModelConsts cs;
+  int sdot[kMaxDot];
+  float sh[kMaxDot];
+  df shd[kMaxDot];
+  df sui[kMaxDot];
+  unsigned blist[128];
+  unsigned bcnt;
+  df rbest[kResolveThreads / 32], rsec[kResolveThreads / 32];
+  unsigned rbits[kResolveThreads / 32];
+};
+
+template <bool CLOSED>
+__device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, ResolveShared& S,
+                                     ListEntry te, unsigned& my_res) {
+  constexpr int L1 = kCheckL1, L2 = kCheckL2;
+  constexpr int NI = 1 << L1;
+  constexpr int NM = 1 << L2;
+  constexpr int NW = kResolveThreads / 32;
+  constexpr unsigned kCap = 128;
+  const float* sM = S.cs.Mhi;
+  const float* sMlo = S.cs.Mlo;
+  const int n = a.n;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  int* sdot = S.sdot;
+  float* sh = S.sh;
+  df* shd = S.shd;
+  df* sui = S.sui;
+  unsigned* blist = S.blist;
+  unsigned& bcnt = S.bcnt;
+  df* rbest = S.rbest;
+  df* rsec = S.rsec;
+  unsigned* rbits = S.rbits;
+  const long long p = te.p;
+  const PixRec* rec = a.recs + p;
+  const unsigned mask = rec->mask;
+  const int k = __popc(mask);
+  const int w = rec->w;
+  // h_i = (M (base - c))_i in double-float, and U(base) = r0 . h / 2
+  if (tid < n) {
+    df hi = {0.f, 0.f};
+    for (int j = 0; j < n; ++j) {
+      const df rj = df_sub({(float)rec->base[j], 0.f}, {rec->chi[j], rec->clo[j]});
+      hi = df_add(hi, df_mul({sM[tid * kLdM + j], sMlo[tid * kLdM + j]}, rj));
+    }
+    const df r0 = df_sub({(float)rec->base[tid], 0.f}, {rec->chi[tid], rec->clo[tid]});
+    sui[tid] = df_mul(hi, r0);
+    if ((mask >> tid) & 1u) {
+      const int s = __popc(mask & ((1u << tid) - 1u));
+      sdot[s] = tid;
+      sh[s] = rec->h[tid];
+      shd[s] = df_add(hi, df_mul_f({sM[tid * kLdM + tid], sMlo[tid * kLdM + tid]}, 0.5f));
+    }
+  }
+  if (tid == 0) bcnt = 0u;
+  __syncthreads();
+  // every block whose FP32 minimum is within the bound of the search's
+  const SlotView sv{sdot, sh, k, w};
+  const float thr = te.m1 + rec->bound;
+  float d1, d2;
+  unsigned db;
+  unsigned long long ev = 0;
+  search_lane<L1, L2, CLOSED, true>(sM, sv, tid, kResolveThreads, thr, blist, &bcnt,
+                                    kCap, d1, db, d2, ev);
+  __syncthreads();
+  const unsigned nb = bcnt;
+  const bool fits = nb <= kCap;
+  df best = {kInf, 0.f}, second = {kInf, 0.f};
+  unsigned bbits = 0xffffffffu;
+  if (fits) {
+    for (unsigned idx = tid; idx < nb * NI; idx += kResolveThreads) {
+      const unsigned id = blist[idx / NI];
+      const unsigned b = idx % NI;
+      const unsigned bits = ((id >> L2) << (L1 + L2)) | ((id & (NM - 1)) << L1) | b;
+      if ((bits >> k) != 0u) continue;
+      if (CLOSED && __popc(bits) != w) continue;
+      df E = {0.f, 0.f};
+      for (unsigned m = bits; m; m &= m - 1u) {
+        const int s = __ffs(m) - 1;
+        const int d = sdot[s];
+        E = df_add(E, shd[s]);
+        for (unsigned q = bits & ((1u << s) - 1u); q; q &= q - 1u) {
+          const int d2i = sdot[__ffs(q) - 1];
+          E = df_add(E, {sM[d * kLdM + d2i], sMlo[d * kLdM + d2i]});
+        }
+      }
+      const bool better = E.hi < best.hi || (E.hi == best.hi && E.lo < best.lo) ||
+                          (E.hi == best.hi && E.lo == best.lo && __brev(bits) < __brev(bbits));
+      if (better) { second = best; best = E; bbits = bits; }
+      else if (E.hi < second.hi || (E.hi == second.hi && E.lo < second.lo)) { second = E; }
+    }
+  }
+  auto less = [](df x, df y) { return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo); };
+  auto merge = [&](df ob, df os, unsigned obb) {
+    const bool take = less(ob, best) ||
+                      (ob.hi == best.hi && ob.lo == best.lo && __brev(obb) < __brev(bbits));
+    const df lose = take ? best : ob;
+    const df s2 = less(os, second) ? os : second;
+    second = less(lose, s2) ? lose : s2;
+    if (take) { best = ob; bbits = obb; }
+  };
+  for (int off = 16; off > 0; off >>= 1) {
+    df ob, os;
+    ob.hi = __shfl_xor_sync(kFull, best.hi, off);
+    ob.lo = __shfl_xor_sync(kFull, best.lo, off);
+    os.hi = __shfl_xor_sync(kFull, second.hi, off);
+    os.lo = __shfl_xor_sync(kFull, second.lo, off);
+    merge(ob, os, __shfl_xor_sync(kFull, bbits, off));
+  }
+  if (lane == 0) { rbest[wid] = best; rsec[wid] = second; rbits[wid] = bbits; }
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 1; i < NW; ++i) merge(rbest[i], rsec[i], rbits[i]);
+    df ub = {0.f, 0.f};
+    for (int i = 0; i < n; ++i) ub = df_add(ub, sui[i]);
+    ub = df_mul_f(ub, 0.5f);
+    const double gap = df_to_double(second) - df_to_double(best);
+    const double eps = 1e-10 * (1.0 + fabs(df_to_double(ub)));
+    if (!fits || bbits == 0xffffffffu || !(gap > eps)) {
+      const unsigned at = atomicAdd(&L.cnt->n_flag, 1u);
+      L.flag_list[at] = ListEntry{te.array, (int)p, te.m1, 0};
+    } else {
+      unsigned flags = (a.out_flags ? a.out_flags[p] : 0u) | kFlagRechecked;
+      for (int i = 0; i < n; ++i) {
+        int ni = rec->base[i];
+        if ((mask >> i) & 1u) ni += (int)((bbits >> __popc(mask & ((1u << i) - 1u))) & 1u);
+        if (ni > 127) { ni = 127; flags |= kFlagOverflow; }
+        a.out_n[p * n + i] = (int8_t)ni;
+      }
+      if (a.out_U) a.out_U[p] = df_to_double(df_add(ub, best));
+      if (a.out_flags) a.out_flags[p] = (uint8_t)flags;
+      my_res += 1;
+    }
+    atomicMax(&L.cnt->shortlist_max, (unsigned long long)nb);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// (a7) FP64 recheck of one list entry (one block per pixel):
+//   1. c, the continuous minimum and the candidate set again, in FP64
+//      (c and h by N threads in parallel, the minimum by one thread);
+//   2. the FP32 search over that set with all threads -> m1;
+//   3. the same search collecting every block whose minimum is within the
+//      near-tie bound of m1 (the exact argmin is guaranteed to be there);
+//   4. exact FP64 energies of those candidates, ties to the
+//      lexicographically smallest charge vector.
+// ---------------------------------------------------------------------------
+struct RecheckShared {
+  float sM[kMaxDot * kLdM];
+  int sdot[kMaxDot];
+  float sh[kMaxDot];
+  double sh64[kMaxDot], sc64[kMaxDot];
+  int sbase[kMaxDot];
+  int sk, sw, sstatus;
+  unsigned smask, sflags;
+  float sbound;
+  float rm1[kRecheckThreads / 32];
+  double re[kRecheckThreads / 32];
+  unsigned rbits[kRecheckThreads / 32];
+  unsigned blist[kBcap];
+  unsigned bcount;
+};
+
+template <bool CLOSED>
+__device__ inline void recheck_entry(const GsLaunch& L, const ArrayDesc& a, RecheckShared& S,
+                                     ListEntry fe) {
+  constexpr int L1 = kCheckL1, L2 = kCheckL2;
+  constexpr int NI = 1 << L1;
+  constexpr int NM = 1 << L2;
+  constexpr int NW = kRecheckThreads / 32;
+  const int n = a.n;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const float* sM = S.sM;
+  int* sdot = S.sdot;
+  float* sh = S.sh;
+  double* sh64 = S.sh64;
+  double* sc64 = S.sc64;
+  int* sbase = S.sbase;
+  int& sk = S.sk;
+  int& sw = S.sw;
+  int& sstatus = S.sstatus;
+  unsigned& smask = S.smask;
+  unsigned& sflags = S.sflags;
+  float& sbound = S.sbound;
+  float* rm1 = S.rm1;
+  double* re = S.re;
+  unsigned* rbits = S.rbits;
+  unsigned* blist = S.blist;
+  unsigned& bcount = S.bcount;
+  const long long p = fe.p;
+  if (tid < n) sc64[tid] = pixel_c_f64(a.md, a.ng, a.sc, a.mt.carrier, p, tid);
+  __syncthreads();
+  if (tid == 0) {
+    double c[kMaxDot];
+    int base[kMaxDot];
+    unsigned mask = 0u, fl = 0u;
+    int w = -1;
+    for (int i = 0; i < n; ++i) c[i] = sc64[i];
+    sstatus = (a.md->status != 0) ? -1 : settle_pixel_f64(a.md, n, a.mt, c, base, mask, w, fl);
+    sflags = fl;
+    smask = mask;
+    sw = CLOSED ? w : -1;
+    for (int i = 0; i < n; ++i) sbase[i] = base[i];
+    bcount = 0u;
+  }
+  __syncthreads();
+  if (sstatus != 0) {
+    if (tid == 0) {
+      if (a.out_flags) a.out_flags[p] |= (uint8_t)kFlagUnresolved;
+      atomicAdd(&L.cnt->unresolved, 1ull);
+    }
+    return;
+  }
+  const unsigned mask = smask;
+  if (tid < n && ((mask >> tid) & 1u)) {
+    double h = 0.0;
+    for (int j = 0; j < n; ++j) h += a.md->M[tid * n + j] * ((double)sbase[j] - sc64[j]);
+    const int s = __popc(mask & ((1u << tid) - 1u));
+    sdot[s] = tid;
+    sh64[s] = h;
+    sh[s] = __double2float_rn(h);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int k = __popc(mask);
+    float S = 0.f;
+    for (int s = 0; s < k; ++s) {
+      S += fabsf(sh[s]) + 0.5f * sM[sdot[s] * kLdM + sdot[s]];
+      for (int q = 0; q < s; ++q) S += fabsf(sM[sdot[s] * kLdM + sdot[q]]);
+    }
+    sk = k;
+    sbound = near_tie_bound(S, k, L2);
+  }
+  __syncthreads();
+  const SlotView sv{sdot, sh, sk, sw};
+  float m1, m2;
+  unsigned b1;
+  unsigned long long ev = 0;
+  search_lane<L1, L2, CLOSED, false>(sM, sv, tid, kRecheckThreads, 0.f, nullptr,
+                                     nullptr, 0u, m1, b1, m2, ev);
+  for (int off = 16; off > 0; off >>= 1) m1 = fminf(m1, __shfl_xor_sync(kFull, m1, off));
+  if (lane == 0) rm1[wid] = m1;
+  __syncthreads();
+  m1 = kInf;
+  for (int i = 0; i < NW; ++i) m1 = fminf(m1, rm1[i]);
+  const float thr = m1 + sbound;
+  float d1, d2;
+  unsigned db;
+  search_lane<L1, L2, CLOSED, true>(sM, sv, tid, kRecheckThreads, thr, blist,
+                                    &bcount, kBcap, d1, db, d2, ev);
+  __syncthreads();
+  const unsigned nb = bcount;
+  const bool overflowed = nb > kBcap;
+  const unsigned nbl = overflowed ? kBcap : nb;
+  // exact FP64 energies of the shortlisted candidates
+  double best = 1.0e300;
+  unsigned bbits = 0xffffffffu;
+  const int k = sk;
+  for (unsigned idx = tid; idx < nbl * NI; idx += kRecheckThreads) {
+    const unsigned id = blist[idx / NI];
+    const unsigned b = idx % NI;
+    const unsigned bits = ((id >> L2) << (L1 + L2)) | ((id & (NM - 1)) << L1) | b;
+    if ((bits >> k) != 0u) continue;
+    if (CLOSED && __popc(bits) != sw) continue;
+    double E = 0.0;
+    for (unsigned m = bits; m; m &= m - 1u) {
+      const int s = __ffs(m) - 1;
+      const int d = sdot[s];
+      E += sh64[s] + 0.5 * a.md->M[d * n + d];
+      for (unsigned q = bits & ((1u << s) - 1u); q; q &= q - 1u)
+        E += a.md->M[d * n + sdot[__ffs(q) - 1]];
+    }
+    if (E < best || (E == best && __brev(bits) < __brev(bbits))) {
+      best = E;
+      bbits = bits;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double oe = __shfl_xor_sync(kFull, best, off);
+    const unsigned ob = __shfl_xor_sync(kFull, bbits, off);
+    if (oe < best || (oe == best && __brev(ob) < __brev(bbits))) { best = oe; bbits = ob; }
+  }
+  if (lane == 0) { re[wid] = best; rbits[wid] = bbits; }
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 1; i < NW; ++i)
+      if (re[i] < best || (re[i] == best && __brev(rbits[i]) < __brev(bbits))) {
+        best = re[i];
+        bbits = rbits[i];
+      }
+    unsigned flags = (a.out_flags ? a.out_flags[p] : 0u) | sflags | kFlagRechecked;
+    if (overflowed || bbits == 0xffffffffu) {
+      flags |= kFlagUnresolved;
+      atomicAdd(&L.cnt->unresolved, 1ull);
+    } else {
+      int nst[kMaxDot];
+      for (int i = 0; i < n; ++i) nst[i] = sbase[i];
+      for (int s = 0; s < k; ++s)
+        if ((bbits >> s) & 1u) nst[sdot[s]] += 1;
+      double U = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double row = 0.0;
+        for (int j = 0; j < n; ++j) row += a.md->M[i * n + j] * ((double)nst[j] - sc64[j]);
+        U += ((double)nst[i] - sc64[i]) * row;
+      }
+      for (int i = 0; i < n; ++i) {
+        int v = nst[i];
+        if (v > 127) { v = 127; flags |= kFlagOverflow; }
+        a.out_n[p * n + i] = (int8_t)v;
+      }
+      if (a.out_U) a.out_U[p] = 0.5 * U;
+    }
+    if (a.out_flags) a.out_flags[p] = (uint8_t)flags;
+    atomicMax(&L.cnt->shortlist_max, (unsigned long long)nb);
+  }
+}
+
+}  // namespace qa

@@ -16,36 +16,63 @@ struct SearchCfg {
   int T;   // lanes per pixel (1..32)
 };
 
-struct GsLaunch {
+// One array of a ground-state call: its model, voltages, method settings,
+// scratch records and outputs.
+struct ArrayDesc {
   const ModelData* md;
   int n, ng;
   Scan sc;
   RasterK rk;          // host-computed raster constants (rk.valid = 0: device)
   Method mt;
   SearchCfg cfg;
-  int prep_team;       // lanes per pixel in the prep kernel (pow2 >= n, <= 16)
+  int prep_team;       // lanes per pixel in the prep stage (pow2 >= n, <= 16)
+  int klass;           // search split class: 0 (2,0), 1 (4,0), 2 (4,3), 3 (5,4)
   float bx_analytic;   // decision margin for double-float continuous minima
-  float bx_qp_scale;   // ... times (1 + max|c| + N_hat) for FP32 QP minima
+  float bx_qp_scale;   // ... per unit of (1 + max|c| + N_hat) for FP32 QP minima
   PixRec* recs;        // scratch [P]
-  int* flag_list;      // scratch [P]: pixels for the FP64 recheck
-  TieEntry* tie_list;  // scratch [P]: near-tie pixels for the resolve kernel
-  Counters* cnt;       // scratch, zeroed at the start of each call
-  BlockCounts* bc_prep;    // scratch [prep blocks]
-  BlockCounts* bc_search;  // scratch [search blocks]
   int8_t* out_n;
   double* out_U;
   uint8_t* out_flags;
-  int num_sms;
-  cudaEvent_t* ev;     // optional: events around setup+prep / search / resolve+recheck
 };
 
-// setup -> prep -> search -> resolve -> FP64 recheck, enqueued on `st`.
+// Pixels [first, first + count) of one array of a batched call.
+struct WorkUnit {
+  int array;
+  int count;
+  long long first;
+};
+
+struct GsLaunch {
+  ArrayDesc one;               // single-array call
+  const ArrayDesc* table;      // batched call: descriptors (null: use `one`)
+  const WorkUnit* prep_units;  // batched call: work queues, largest first
+  int n_prep_units;
+  const WorkUnit* search_units;
+  int n_search_units;
+  ListEntry* flag_list;        // scratch: pixels for the FP64 recheck
+  ListEntry* tie_list;         // scratch: near-tie pixels for the resolve kernel
+  Counters* cnt;               // scratch, zeroed at the start of each call
+  BlockCounts* bc_prep;        // scratch [prep blocks]
+  BlockCounts* bc_search;      // scratch [search blocks]
+  int grid_prep, grid_search;  // batched call: persistent grid sizes
+  int num_sms;
+  cudaEvent_t* ev;     // optional: events around prep / search / resolve+recheck
+};
+
+// prep -> search -> resolve -> FP64 recheck of one array, enqueued on `st`.
 cudaError_t launch_ground_state(const GsLaunch& a, cudaStream_t st);
+// The same for a batch (persistent kernels over the work queues).
+cudaError_t launch_ground_state_batch(const GsLaunch& a, cudaStream_t st);
 // prep alone (candidate-set records), for the soft path.
 cudaError_t launch_prep(const GsLaunch& a, cudaStream_t st);
+// resolve + FP64 recheck over the lists of a call (single or batched).
+cudaError_t launch_lists(const GsLaunch& a, cudaStream_t st);
 int prep_blocks(const GsLaunch& a);
 int search_blocks(const GsLaunch& a);
 bool search_cfg_supported(const SearchCfg& c);
+int search_klass(const SearchCfg& c);
+// Resident blocks per SM of the persistent batched kernels.
+void batch_occupancy(int* prep_per_sm, int* search_per_sm);
 
 struct SoftLaunch {
   const ModelData* md;

@@ -1,0 +1,74 @@
+"""The batched ground state (persistent launches over a device work queue)
+against the single-array calls and the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_04994_gb300 import inputs
+from parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed_specs(count, sides=(12, 17), seed=0, nmax=16):
+    r = np.random.Generator(np.random.PCG64(4242 + seed))
+    specs = []
+    for a in range(count):
+        n = int(r.integers(2, nmax + 1))
+        Cdd = inputs.grid_cdd(r, 4, 4) if n == 16 else inputs.chain_cdd(r, n, nn=(0.05, 0.25))
+        Cgd = inputs.dense_cgd(r, n, diag=(0.5, 1.0), off=(0.0, 0.1))
+        gx, gy = inputs.swept_gates(n)
+        V = inputs.offsets(r, n, (gx, gy))
+        side = int(sides[int(r.integers(0, len(sides)))])
+        closed = bool(r.integers(0, 2))
+        t = float(r.choice([1.0, 1.0, 0.5]))
+        specs.append(dict(Cdd=Cdd, Cgd=Cgd, raster=inputs.raster(n, gx, gy, V, W=side, H=side - 3),
+                          threshold=t, closed=closed, n_charges=n if closed else 0))
+    return specs
+
+
+def test_batch_matches_oracle_and_single_calls(qa):
+    specs = _mixed_specs(40)
+    b = qa.Batch(specs)
+    b.run()
+    st = b.stats()
+    assert st["pixels"] == sum(s["raster"]["W"] * s["raster"]["H"] for s in specs)
+    assert st["unresolved"] == 0
+    for sp, (n, U, f) in zip(specs, b.outputs):
+        nd = sp["Cdd"].shape[0]
+        n = n.cpu().numpy().reshape(-1, nd)
+        U = U.cpu().numpy().reshape(-1)
+        f = f.cpu().numpy().reshape(-1)
+        rec = oracle.ground_state(sp["Cdd"], sp["Cgd"], raster=sp["raster"], t=sp["threshold"],
+                                  closed=sp["closed"], n_charges=sp["n_charges"])
+        compare(n, U, f, rec, sp["Cdd"], f"batch N={nd} closed={sp['closed']}")
+        m = qa.Model(sp["Cdd"], sp["Cgd"])
+        if sp["closed"]:
+            n1, U1, _ = m.ground_state_closed(sp["raster"], sp["n_charges"], threshold=sp["threshold"])
+        else:
+            n1, U1, _ = m.ground_state_open(sp["raster"], threshold=sp["threshold"])
+        np.testing.assert_array_equal(n, n1.cpu().numpy().reshape(-1, nd))
+        np.testing.assert_allclose(U, U1.cpu().numpy(), rtol=1e-9, atol=1e-12)
+        m.close()
+    b.close()
+
+
+def test_batch_rerun_and_team_override(qa):
+    specs = _mixed_specs(10, sides=(20,), seed=1)
+    for sp in specs:
+        sp["team"] = 4
+    b = qa.Batch(specs)
+    b.run()
+    first = [o[0].clone() for o in b.outputs]
+    b.run()
+    for o, f0 in zip(b.outputs, first):
+        assert bool((o[0] == f0).all())
+    b.close()
+
+
+def test_batch_rejects_bad_items(qa):
+    sp = _mixed_specs(1)[0]
+    sp["threshold"] = 2.0
+    with pytest.raises(qa.QAError) as e:
+        qa.Batch([sp])
+    assert e.value.code == -5
