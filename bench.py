@@ -328,6 +328,7 @@ def extra_measurements(api, torch, flush, args):
             ms = timed(lambda: m.ground_state_open(c["raster"]))
         out[f"{name}_pixels_per_s"] = P / (ms * 1e-3)
         m.close()
+    out.update(batch_measurements(api, torch, flush))
     try:
         from paper_2404_04994_gb300 import autograd as qag
         for kT in (0.01, 0.05):
@@ -336,6 +337,64 @@ def extra_measurements(api, torch, flush, args):
             out[f"grad_step_ms_grid8_kT{kT:g}"] = ms_step
     except ImportError:
         pass
+    return out
+
+
+def batch_measurements(api, torch, flush):
+    """The 4096-array batch (N ~ U{2..16}, 64^2 / 128^2 rasters, open or
+    closed with N_hat = N): one graph-captured batched run versus the plain
+    form (one single-array call per array), pixels/s of each."""
+    from paper_2404_04994_gb300 import inputs
+    specs = inputs.batch(4096)
+    b = api.Batch(specs)
+    b.run()
+    torch.cuda.synchronize()
+    st = b.stats()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.run(s)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.run()
+    times = []
+    for _ in range(3):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms_batch = min(times)
+    # plain form: one call per array, outputs preallocated, after a warm-up pass
+    def plain():
+        for sp, m, (n, U, f) in zip(specs, b.models, b.outputs):
+            if sp["closed"]:
+                api.qa_ground_state_closed(m.handle, sp["raster"], sp["t"], sp["n_charges"],
+                                           n, U, f)
+            else:
+                api.qa_ground_state_open(m.handle, sp["raster"], sp["t"], n, U, f)
+    plain()
+    torch.cuda.synchronize()
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plain()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    out = {"batch4096_pixels": b.pixels, "batch4096_ms": ms_batch,
+           "batch4096_pixels_per_s": b.pixels / (ms_batch * 1e-3),
+           "batch4096_plain_ms": ms_plain,
+           "batch4096_plain_pixels_per_s": b.pixels / (ms_plain * 1e-3),
+           "batch4096_candidates": st["candidates"], "batch4096_flagged": st["flagged"],
+           "batch4096_unresolved": st["unresolved"]}
+    del g
+    b.close()
     return out
 
 
