@@ -90,6 +90,27 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------
+def search_traffic():
+    """dram read+write bytes per launch of the search kernel from the committed
+    ncu summary, or None when the kernel sources changed since that capture."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles", "search_kernel_grid16_100x100.md")
+    if not os.path.exists(prof):
+        return None
+    text = open(prof).read()
+    m_hash = re.search(r"kernel_source_sha256_16: ([0-9a-f]{16})", text)
+    m_traf = re.search(r"\| traffic_bytes_per_launch \| (\d+) \|", text)
+    if not (m_hash and m_traf):
+        return None
+    csrc = os.path.join(ROOT, "paper_2404_04994_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("qa_search.cuh", "qa_gs_tiles.cuh", "qa_kernels_gs.cu", "qa_device.cuh",
+              "qa_prep.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return int(m_traf.group(1)) if h.hexdigest()[:16] == m_hash.group(1) else None
+
+
 def workload(rank=0):
     from paper_2404_04994_gb300 import inputs
     cfg = inputs.grid16(W=100, H=100, t=1.0)
@@ -229,7 +250,7 @@ def run_ours(args):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = n_sm * 128 * sm_max * 1e6 / 1e12   # FP32 lanes x clock
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
-                "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": search_traffic(),
                 "kernel": "k_search<5,4,open>", "ops_per_launch": ops,
                 "ops_per_evaluated_slot": ops_per_slot,
                 "search_ms": round(ms_s, 5), "prep_ms": round(statistics.mean(prep_ms), 5),

@@ -101,9 +101,9 @@ typedef struct {
     long long candidates;      /* admissible candidates (2^k or C(k, w))      */
     long long evaluated;       /* candidate energies evaluated by the kernels */
     long long qp_pixels;       /* pixels that needed the QP                   */
-    long long flagged;         /* pixels queued for the FP64 recheck          */
-    long long near_tie;        /* ... because of the top-two gap              */
-    long long boundary;        /* ... because of a decision boundary / QP cap */
+    long long flagged;         /* pixels re-evaluated exactly: the two below  */
+    long long near_tie;        /* FP32 top-two gap under the bound (resolve)  */
+    long long boundary;        /* decision boundary / QP cap (FP64 recheck)   */
     long long unresolved;      /* pixels the recheck could not settle         */
     long long overflow;        /* pixels whose charges exceed int8            */
     long long doubled;         /* closed pixels whose threshold was doubled   */

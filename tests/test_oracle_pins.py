@@ -166,8 +166,11 @@ def test_uncoupled_dots_round_and_clip(t):
     n = 5
     d = rng.uniform(0.5, 2.0, n)
     Cdd = np.diag(d)
-    Cgd = np.diag(rng.uniform(0.5, 1.0, n))
-    V = rng.uniform(-2.0, 8.0, size=(300, n))
+    # dense, non-square gate matrix: a transposed or mis-indexed Cgd changes c
+    ng = n + 2
+    Cgd = rng.uniform(0.0, 0.3, size=(n, ng))
+    Cgd[np.arange(n), np.arange(n)] += rng.uniform(0.5, 1.0, n)
+    V = rng.uniform(-2.0, 8.0, size=(300, ng))
     out = oracle.ground_state(Cdd, Cgd, V=V, t=t)
     c = V @ Cgd.T
     expect = np.maximum(0, np.floor(c + 0.5)).astype(int)
