@@ -137,6 +137,32 @@ __device__ __forceinline__ float state_from_scratch(const float* sM,
   return A;
 }
 
+// Adds the slots of add_bits to a rest state (A, q, gm).  Each added slot
+// pairs with every set slot of all_bits below it, so adding disjoint slot sets
+// in increasing slot order, with all_bits holding everything below, gives the
+// same state as state_from_scratch of the union (up to summation order: every
+// value is still a sum of at most 2k rounded terms).  M is symmetric, so the
+// middle gradients gm_m = g_m + sum_s M_{m s} come from the same row.
+template <int L1, int L2>
+__device__ __forceinline__ void state_add(const float* sM, const SlotView& sv,
+                                          unsigned all_bits, unsigned add_bits,
+                                          const int* dI, const int* dM,
+                                          float& A, float* q, float* gm) {
+  for (unsigned bits = add_bits; bits; bits &= bits - 1u) {
+    const int s = __ffs(bits) - 1;
+    const int d = sv.dot[s];
+    const float* Mrow = sM + d * kLdM;
+    float add = sv.h[s] + 0.5f * Mrow[d];
+    for (unsigned prev = all_bits & ((1u << s) - 1u); prev; prev &= prev - 1u)
+      add += Mrow[sv.dot[__ffs(prev) - 1]];
+    A += add;
+#pragma unroll
+    for (int j = 0; j < L1; ++j) q[j] += Mrow[dI[j]];
+#pragma unroll
+    for (int m = 0; m < L2; ++m) gm[m] += Mrow[dM[m]];
+  }
+}
+
 // Search of one lane's share.  Lane t of a team of T handles the outer
 // patterns o = t, t + T, ...; results: best energy m1 with its full slot
 // pattern b1, and the second-best energy m2 over the lane's candidates.
@@ -208,26 +234,41 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
     for (int m = 0; m < L2; ++m)
       Mim[j][m] = (m < nmid) ? sM[dI[j] * kLdM + dM[m]] : 0.f;
 
+  // Outer patterns o = t + T i: the low log2(T) bits of o are the lane's own
+  // and fixed, so the lane-bit part of the rest state is built once and each
+  // iteration only adds its iteration bits.
   const int nout = max(k - L1 - L2, 0);
-  const unsigned nouter = 1u << nout;
+  const int nlb = min(__ffs(T) - 1, nout);
+  const int nit = nout - nlb;
   float g1 = kInf, g2 = kInf;
   unsigned blk = 0u;
-  unsigned long long nblocks = 0;
+  const int nsteps = 1 << nmid;  // Gray steps that stay inside the k slots
+  const unsigned niter = ((unsigned)t < (1u << nlb)) ? (1u << nit) : 0u;
+  float At = 0.f;
+  float qt[L1 > 0 ? L1 : 1];
+  float gt[L2 > 0 ? L2 : 1];
+#pragma unroll
+  for (int j = 0; j < L1; ++j) qt[j] = qb[j];
+#pragma unroll
+  for (int m = 0; m < L2; ++m) gt[m] = gb[m];
+  if (niter) {
+    const unsigned lane_bits = (unsigned)t << (L1 + L2);
+    state_add<L1, L2>(sM, sv, lane_bits, lane_bits, dI, dM, At, qt, gt);
+  }
 
-  for (unsigned o = (unsigned)t; o < nouter; o += (unsigned)T) {
-    float q[L1 > 0 ? L1 : 1];
+  for (unsigned it = 0; it < niter; ++it) {
+    const unsigned o = (unsigned)t | (it << nlb);
     const unsigned obits = o << (L1 + L2);
-    float A = state_from_scratch<L1>(sM, sv, obits, dI, qb, q);
+    float A = At;
+    float q[L1 > 0 ? L1 : 1];
     float gm[L2 > 0 ? L2 : 1];
 #pragma unroll
-    for (int m = 0; m < L2; ++m) {
-      float e = gb[m];
-      for (unsigned bits = obits; bits; bits &= bits - 1u)
-        e += sM[dM[m] * kLdM + sv.dot[__ffs(bits) - 1]];
-      gm[m] = e;
-    }
+    for (int j = 0; j < L1; ++j) q[j] = qt[j];
+#pragma unroll
+    for (int m = 0; m < L2; ++m) gm[m] = gt[m];
+    state_add<L1, L2>(sM, sv, obits, (it << nlb) << (L1 + L2), dI, dM, A, q, gm);
+    const unsigned obase = o << L2;
     const int popo = __popc(o);
-    const int nsteps = 1 << nmid;  // Gray steps that stay inside the k slots
 #pragma unroll
     for (int s = 0; s < NM; ++s) {
       // Guarded rather than `break`: the walk must stay fully unrolled so that
@@ -251,8 +292,7 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
         const int r = sv.w - popo - popc_c(gray_c((unsigned)s));
         mbk = inner_min_closed<L1>(A, q, P, r);
       }
-      ++nblocks;
-      const unsigned id = (o << L2) | gray_c((unsigned)s);
+      const unsigned id = obase | gray_c((unsigned)s);
       if (COLLECT) {
         if (mbk <= thr) {
           const unsigned at = atomicAdd(bcount, 1u);
@@ -266,7 +306,7 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
       }
     }
   }
-  evaluated += nblocks * (unsigned long long)NI;
+  evaluated += (unsigned long long)niter * (unsigned)nsteps * (unsigned)NI;
   if (COLLECT) return;
 
   m1 = kInf;
