@@ -79,6 +79,16 @@ def test_grid16_full_size_sampled_rows(qa, t):
     assert st["unresolved"] == 0
 
 
+def test_grid16_full_diagram_every_pixel(qa):
+    # the benchmark's diagram, all 10^4 pixels against the oracle: checks the
+    # FP32 near-tie bound of the search on every comparable pixel
+    cfg = inputs.grid16(t=1.0)
+    n, U, f, st = _gpu(qa, cfg)
+    rep = compare(n, U, f, _oracle(cfg), cfg["Cdd"], "grid16 100x100 t=1")
+    assert rep["comparable"] >= 9900
+    assert st["unresolved"] == 0
+
+
 @pytest.mark.parametrize("t", [1.0, 0.6, 0.25, 0.0])
 def test_closed_threshold_doubling(qa, t):
     cfg = inputs.chain4(W=33, H=29, closed=True)
