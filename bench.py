@@ -416,6 +416,43 @@ def batch_measurements(api, torch, flush):
            "batch4096_unresolved": st["unresolved"]}
     del g
     b.close()
+    # autotuned: threshold and team per (N, form) from 24 x 24 samples
+    from paper_2404_04994_gb300 import autotune
+    import time
+    t0 = time.perf_counter()
+    table = autotune.tune(specs, sample_side=24, arrays_per_group=4)
+    tune_s = time.perf_counter() - t0
+    tb = api.Batch(autotune.apply(specs, table))
+    tb.run()
+    torch.cuda.synchronize()
+    gt = torch.cuda.CUDAGraph()
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s2):
+        tb.run(s2)
+    torch.cuda.current_stream().wait_stream(s2)
+    with torch.cuda.graph(gt):
+        tb.run()
+    tt = []
+    for _ in range(3):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gt.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        tt.append(e0.elapsed_time(e1))
+    tst = tb.stats()
+    out.update({"batch4096_tuned_ms": min(tt),
+                "batch4096_tuned_pixels_per_s": tb.pixels / (min(tt) * 1e-3),
+                "batch4096_tuned_candidates": tst["candidates"],
+                "batch4096_tuned_unresolved": tst["unresolved"],
+                "autotune_s": tune_s,
+                "autotune_table": {f"{'closed' if c else 'open'}{n}": [e["threshold"], e["team"]]
+                                   for (n, c), e in sorted(table.items())}})
+    del gt
+    tb.close()
     return out
 
 

@@ -886,20 +886,32 @@ int qa_batch_create(const qa_batch_item* items, int count, qa_batch** out) {
   }
   if (rc) { delete b; return rc; }
   b->count = count;
-  // work units: prep in runs of ~4096 pixels; search in runs worth about
-  // 2^18 candidate evaluations, largest first
+  // work units, sized so that the persistent grids get several units per
+  // block however the pixels are spread over the arrays: prep in runs of at
+  // most 4096 pixels, search in runs of about an equal share of the total
+  // candidate work (2^14 to 2^18 evaluations, at most 64 tiles), largest first
+  if ((rc = select_device(items[0].model))) { delete b; return rc; }
+  int pps = 1, sps = 1;
+  qa::batch_occupancy(&pps, &sps);
+  const double unit_target = 8.0;  // units per resident block
+  double total_cost = 0.0;
+  for (int i = 0; i < count; ++i) total_cost += unit_cost(table[(size_t)i]) * (double)b->P[(size_t)i];
+  const long long prep_share =
+      (long long)std::ceil((double)b->pixels / (unit_target * b->num_sms * pps));
+  const double search_share =
+      std::min(262144.0, std::max(16384.0, total_cost / (unit_target * b->num_sms * sps)));
   std::vector<qa::WorkUnit> pu, su;
   std::vector<double> scost;
   for (int i = 0; i < count; ++i) {
     const qa::ArrayDesc& d = table[(size_t)i];
     const long long P = b->P[(size_t)i];
     const long long tpb = 128 / d.prep_team;
-    const long long pchunk = std::max(tpb, (4096 / tpb) * tpb);
+    const long long pchunk = std::max(tpb, std::min(4096LL / tpb, (prep_share + tpb - 1) / tpb) * tpb);
     for (long long f = 0; f < P; f += pchunk)
       pu.push_back({i, (int)std::min(pchunk, P - f), f});
     const long long teams = 128 / d.cfg.T;
     const double c = unit_cost(d);
-    long long k = (long long)std::max(1.0, std::floor(262144.0 / (c * (double)teams)));
+    long long k = (long long)std::max(1.0, std::floor(search_share / (c * (double)teams)));
     k = std::min(k, 64LL);
     const long long schunk = teams * k;
     for (long long f = 0; f < P; f += schunk) {
@@ -915,9 +927,6 @@ int qa_batch_create(const qa_batch_item* items, int count, qa_batch** out) {
   std::vector<qa::WorkUnit> su_sorted(su.size());
   for (size_t i = 0; i < order.size(); ++i) su_sorted[i] = su[order[i]];
 
-  if ((rc = select_device(items[0].model))) { delete b; return rc; }
-  int pps = 1, sps = 1;
-  qa::batch_occupancy(&pps, &sps);
   const int grid_prep = b->num_sms * pps, grid_search = b->num_sms * sps;
   const size_t Ptot = (size_t)std::max(1LL, b->pixels);
   const size_t off_cnt = 0;

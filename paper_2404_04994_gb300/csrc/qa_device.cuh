@@ -157,7 +157,7 @@ struct ListEntry {
   int array;
   int p;
   float m1;
-  int pad;
+  int tie;  // 1 when the order of the best two candidates is in doubt
 };
 
 // Copy the model's FP32 constants into shared memory (16-byte vectors).

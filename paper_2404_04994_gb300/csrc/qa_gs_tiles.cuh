@@ -391,7 +391,7 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
       if (flags & (kFlagBoundary | kFlagQPCap | kFlagUnresolved)) {
         // the candidate set itself may be wrong: FP64 recheck
         const unsigned at = atomicAdd(&L.cnt->n_flag, 1u);
-        L.flag_list[at] = ListEntry{array, (int)p, m1, 0};
+        L.flag_list[at] = ListEntry{array, (int)p, m1, (flags & kFlagNearTie) ? 1 : 0};
         my_bd = 1;
       } else if (flags & kFlagNearTie) {
         // right set, uncertain order: exact energies of the close candidates
@@ -551,7 +551,7 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
     const double eps = 1e-10 * (1.0 + fabs(df_to_double(ub)));
     if (!fits || bbits == 0xffffffffu || !(gap > eps)) {
       const unsigned at = atomicAdd(&L.cnt->n_flag, 1u);
-      L.flag_list[at] = ListEntry{te.array, (int)p, te.m1, 0};
+      L.flag_list[at] = ListEntry{te.array, (int)p, te.m1, 1};
     } else {
       unsigned flags = (a.out_flags ? a.out_flags[p] : 0u) | kFlagRechecked;
       for (int i = 0; i < n; ++i) {
@@ -571,7 +571,10 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
 // ---------------------------------------------------------------------------
 // (a7) FP64 recheck of one list entry (one block per pixel):
 //   1. c, the continuous minimum and the candidate set again, in FP64
-//      (c and h by N threads in parallel, the minimum by one thread);
+//      (c and h by N threads in parallel, the minimum by one thread); when
+//      that set is the one the FP32 path searched and the FP32 order of the
+//      best two was certain, the search's result stands and the pixel is
+//      done;
 //   2. the FP32 search over that set with all threads -> m1;
 //   3. the same search collecting every block whose minimum is within the
 //      near-tie bound of m1 (the exact argmin is guaranteed to be there);
@@ -635,8 +638,18 @@ __device__ inline void recheck_entry(const GsLaunch& L, const ArrayDesc& a, Rech
     sw = CLOSED ? w : -1;
     for (int i = 0; i < n; ++i) sbase[i] = base[i];
     bcount = 0u;
+    // same candidate set as the FP32 search and a certain order: keep its result
+    const PixRec* rec = a.recs + p;
+    bool same = sstatus == 0 && fe.tie == 0 && mask == (unsigned)rec->mask &&
+                (!CLOSED || w == (int)rec->w);
+    for (int i = 0; i < n && same; ++i) same = base[i] == (int)rec->base[i];
+    if (same) {
+      if (a.out_flags) a.out_flags[p] = (uint8_t)(a.out_flags[p] | fl | kFlagRechecked);
+      sstatus = 1;
+    }
   }
   __syncthreads();
+  if (sstatus == 1) return;
   if (sstatus != 0) {
     if (tid == 0) {
       if (a.out_flags) a.out_flags[p] |= (uint8_t)kFlagUnresolved;

@@ -125,3 +125,31 @@ def test_full_size_batch_graph_sampled_against_oracle(qa):
             compared += rep["comparable"]
     assert compared > 0.9 * sum(3 * specs[a]["raster"]["W"] for a in chosen)
     b.close()
+
+
+def test_autotuned_batch_matches_oracle_at_the_tuned_thresholds(qa):
+    from paper_2404_04994_gb300 import autotune
+    specs = _mixed_specs(24, sides=(16, 21), seed=3, nmax=10)
+    for sp in specs:
+        sp["threshold"] = 1.0
+    table = autotune.tune(specs, sample_side=16, arrays_per_group=3)
+    for key, e in table.items():
+        assert e["team"] in autotune.TEAMS
+        if e["threshold"] < 1.0:
+            base = [dict(autotune.sample_spec(specs[i], 16), threshold=1.0) for i in e["arrays"]]
+            ref, _ = autotune.gpu_runner(base, 1)
+            got, _ = autotune.gpu_runner([dict(b, threshold=e["threshold"]) for b in base], 1)
+            for r, g in zip(ref, got):
+                np.testing.assert_array_equal(r, g)
+    tuned = autotune.apply(specs, table)
+    b = qa.Batch(tuned)
+    b.run()
+    assert b.stats()["unresolved"] == 0
+    for sp, (n, U, f) in zip(tuned, b.outputs):
+        nd = sp["Cdd"].shape[0]
+        rec = oracle.ground_state(sp["Cdd"], sp["Cgd"], raster=sp["raster"], t=sp["threshold"],
+                                  closed=sp["closed"], n_charges=sp["n_charges"])
+        compare(n.cpu().numpy().reshape(-1, nd), U.cpu().numpy().reshape(-1),
+                f.cpu().numpy().reshape(-1), rec, sp["Cdd"],
+                f"tuned N={nd} t={sp['threshold']:.3f} team={sp['team']}")
+    b.close()
