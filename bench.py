@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -315,6 +316,8 @@ def run_ours(args):
 def extra_measurements(api, torch, flush, args):
     """Secondary numbers (not the headline): thresholded search, smaller
     arrays, the soft occupation and one gradient step."""
+    import numpy as np
+
     from paper_2404_04994_gb300 import inputs
     out = {}
 
@@ -348,6 +351,19 @@ def extra_measurements(api, torch, flush, args):
         else:
             ms = timed(lambda: m.ground_state_open(c["raster"]))
         out[f"{name}_pixels_per_s"] = P / (ms * 1e-3)
+        # the brute-force row of Table I on the same raster, for comparison
+        r = c["raster"]
+        corners = [np.asarray(r["V0"]) + x * np.asarray(r["u"]) + y * np.asarray(r["w"])
+                   for x in (r["x0"], r["x1"]) for y in (r["y0"], r["y1"])]
+        cmax = max(float(np.max(np.asarray(c["Cgd"]) @ v)) for v in corners)
+        nmax = int(math.ceil(max(cmax, 0.0))) + 2
+        if closed:
+            ms_b = timed(lambda: m.brute_force_closed(r, 4), reps=5)
+        else:
+            ms_b = timed(lambda: m.brute_force_open(r, nmax), reps=5)
+        out[f"{name}_brute_force_pixels_per_s"] = P / (ms_b * 1e-3)
+        if not closed:
+            out[f"{name}_brute_force_n_max"] = nmax
         m.close()
     out.update(batch_measurements(api, torch, flush))
     try:

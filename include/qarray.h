@@ -180,6 +180,26 @@ int qa_ground_state_points(qa_model* m, const double* V_dev, long long P,
                            int8_t* out_n, double* out_U, uint8_t* out_flags,
                            void* stream);
 
+/* Brute-force ground state (Table I, brute-force row; the reference the
+ * default and thresholded methods are measured against in Sec. VII, Fig. 4):
+ * the exact argmin of U over every n in [0, n_max]^n_dot, in FP64, ties to
+ * the lexicographically smallest n.  (n_max + 1)^n_dot states per pixel (at
+ * most 2^40, else QA_ERR_RANGE); 0 <= n_max <= 127.  Outputs as
+ * qa_ground_state_open, with out_flags holding QA_BF_* bits:
+ *   QA_BF_NEAR_TIE  the best two energies are within 1e-9 max(1, |U|);
+ *   QA_BF_AT_BOX    some n_i = n_max (the box may cut off the true minimum). */
+#define QA_BF_NEAR_TIE 1
+#define QA_BF_AT_BOX   2
+int qa_brute_force_open(qa_model* m, const qa_raster* r, int n_max, int8_t* out_n,
+                        double* out_U, uint8_t* out_flags, void* stream);
+
+/* Brute-force ground state of a CLOSED array: every n >= 0 with
+ * sum n = n_charges (constraint iii), in FP64; 0 <= n_charges <= 127 and at
+ * most 2^40 states (n_charges + 1)^(n_dot - 1) per pixel.  Outputs and flags
+ * as qa_brute_force_open (QA_BF_AT_BOX never set). */
+int qa_brute_force_closed(qa_model* m, const qa_raster* r, int n_charges, int8_t* out_n,
+                          double* out_U, uint8_t* out_flags, void* stream);
+
 /* Finite-temperature occupation (Sec. IV.B, Eq. "softargmin") over the
  * method's candidate set at threshold t (closed: states with sum N_hat only):
  *   <n> = sum_c n_c exp(-U_c / kT) / Z,  log Z = log sum_c exp(-U_c / kT),

@@ -115,6 +115,12 @@ def _load():
         lib.qo_brute_force.argtypes = [ctypes.c_int, D, D, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int, I, D, I]
         lib.qo_brute_force.restype = ctypes.c_long
+        lib.qo_brute_force2.argtypes = [ctypes.c_int, D, D, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int)]
+        lib.qo_brute_force2.restype = ctypes.c_long
         _lib = lib
     return _lib
 
@@ -295,3 +301,29 @@ def brute_force(M, c, closed=False, n_charges=0, n_max=3):
                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                  ctypes.byref(U), ctypes.byref(hit))
     return out, U.value, bool(hit.value), int(cnt)
+
+
+def brute_force_raster(Cdd, Cgd, raster, closed=False, n_charges=0, n_max=3, carrier=1.0):
+    """Brute force on every pixel of a raster: dict of n [P, N], U [P],
+    U2 [P] (second-lowest energy) and hit [P] (open argmin at n_max)."""
+    Cdd = np.ascontiguousarray(Cdd, dtype=np.float64)
+    M, _ = _d(inverse_spd(Cdd))
+    n = Cdd.shape[0]
+    P = int(raster["W"]) * int(raster["H"])
+    res = {"n": np.zeros((P, n), dtype=np.int64), "U": np.zeros(P), "U2": np.zeros(P),
+           "hit": np.zeros(P, dtype=bool)}
+    out = np.zeros(n, dtype=np.int32)
+    U = ctypes.c_double(0.0)
+    U2 = ctypes.c_double(0.0)
+    hit = ctypes.c_int(0)
+    for p in range(P):
+        c, pc = _d(raster_c(Cgd, raster, p, carrier=carrier))
+        _load().qo_brute_force2(n, M.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pc,
+                                int(closed), int(n_charges), int(n_max),
+                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                ctypes.byref(U), ctypes.byref(U2), ctypes.byref(hit))
+        res["n"][p] = out
+        res["U"][p] = U.value
+        res["U2"][p] = U2.value
+        res["hit"][p] = bool(hit.value)
+    return res

@@ -649,9 +649,18 @@ long qo_brute_force(int n, const double* M, const double* c, int closed,
                     int n_charges, int n_max, int* out_n, double* out_U,
                     int* hit_nmax)
 {
+    double second;
+    return qo_brute_force2(n, M, c, closed, n_charges, n_max, out_n, out_U,
+                           &second, hit_nmax);
+}
+
+long qo_brute_force2(int n, const double* M, const double* c, int closed,
+                     int n_charges, int n_max, int* out_n, double* out_U,
+                     double* out_U2, int* hit_nmax)
+{
     int hi = closed ? n_charges : n_max;
     int nv[N] = {0};
-    double best = INFINITY;
+    double best = INFINITY, second = INFINITY;
     long count = 0;
     *hit_nmax = 0;
     for (;;) {
@@ -665,8 +674,11 @@ long qo_brute_force(int n, const double* M, const double* c, int closed,
         if (ok) {
             double U = qo_energy(n, M, nv, c);
             if (U < best || (U == best && lex_less(n, nv, out_n))) {
+                second = best;
                 best = U;
                 memcpy(out_n, nv, sizeof(int) * (size_t)n);
+            } else if (U < second) {
+                second = U;
             }
         }
         /* odometer over [0, hi]^n in lexicographic order */
@@ -676,6 +688,7 @@ long qo_brute_force(int n, const double* M, const double* c, int closed,
         ++nv[i];
     }
     *out_U = best;
+    *out_U2 = second;
     if (!closed)
         for (int i = 0; i < n; ++i)
             if (out_n[i] == n_max) *hit_nmax = 1;

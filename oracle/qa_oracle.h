@@ -115,6 +115,12 @@ long qo_brute_force(int n, const double* M, const double* c, int closed,
                     int n_charges, int n_max, int* out_n, double* out_U,
                     int* hit_nmax);
 
+/* The same, also returning the second-lowest energy over the admissible
+ * states (INFINITY when there is only one). */
+long qo_brute_force2(int n, const double* M, const double* c, int closed,
+                     int n_charges, int n_max, int* out_n, double* out_U,
+                     double* out_U2, int* hit_nmax);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,6 +105,8 @@ def load():
                                        I, P, P, P, P]),
         "qa_ground_state_points": (I, [P, P, ctypes.c_longlong, ctypes.c_double, I, I,
                                        P, P, P, P]),
+        "qa_brute_force_open": (I, [P, ctypes.POINTER(qa_raster), I, P, P, P, P]),
+        "qa_brute_force_closed": (I, [P, ctypes.POINTER(qa_raster), I, P, P, P, P]),
         "qa_soft_occupation": (I, [P, ctypes.POINTER(qa_raster), ctypes.c_double,
                                    ctypes.c_double, I, I, P, P, P]),
         "qa_soft_occupation_backward": (I, [P, ctypes.POINTER(qa_raster),
@@ -293,6 +295,33 @@ def qa_ground_state_points(m, V, threshold, closed, n_charges, out_n, out_U=None
         _dev(out_flags, torch.uint8, P, "out_flags"), _stream(stream)))
 
 
+BF_NEAR_TIE = 1
+BF_AT_BOX = 2
+
+
+def qa_brute_force_open(m, raster, n_max, out_n, out_U=None, out_flags=None, stream=None):
+    import torch
+    n, ng = qa_model_shape(m)
+    r = make_raster(raster, ng)
+    P = r.W * r.H
+    _check(load().qa_brute_force_open(
+        m, ctypes.byref(r), int(n_max), _dev(out_n, torch.int8, P * n, "out_n"),
+        _dev(out_U, torch.float64, P, "out_U"),
+        _dev(out_flags, torch.uint8, P, "out_flags"), _stream(stream)))
+
+
+def qa_brute_force_closed(m, raster, n_charges, out_n, out_U=None, out_flags=None,
+                          stream=None):
+    import torch
+    n, ng = qa_model_shape(m)
+    r = make_raster(raster, ng)
+    P = r.W * r.H
+    _check(load().qa_brute_force_closed(
+        m, ctypes.byref(r), int(n_charges), _dev(out_n, torch.int8, P * n, "out_n"),
+        _dev(out_U, torch.float64, P, "out_U"),
+        _dev(out_flags, torch.uint8, P, "out_flags"), _stream(stream)))
+
+
 def qa_soft_occupation(m, raster, kT, threshold, closed, n_charges, out_mean,
                        out_logZ=None, stream=None):
     import torch
@@ -380,6 +409,18 @@ class Model:
         qa_ground_state_points(self.handle, V, threshold, closed, n_charges, n, U, f,
                                stream)
         return n, U, f
+
+    def brute_force_open(self, raster, n_max, energies=True, flags=True, stream=None):
+        P = int(raster["W"]) * int(raster["H"])
+        n, U, f = self._outs(P, energies, flags)
+        qa_brute_force_open(self.handle, raster, n_max, n, U, f, stream)
+        return n.view(int(raster["H"]), int(raster["W"]), self.n_dot), U, f
+
+    def brute_force_closed(self, raster, n_charges, energies=True, flags=True, stream=None):
+        P = int(raster["W"]) * int(raster["H"])
+        n, U, f = self._outs(P, energies, flags)
+        qa_brute_force_closed(self.handle, raster, n_charges, n, U, f, stream)
+        return n.view(int(raster["H"]), int(raster["W"]), self.n_dot), U, f
 
     def soft_occupation(self, raster, kT, threshold=1.0, closed=False, n_charges=0,
                         stream=None):

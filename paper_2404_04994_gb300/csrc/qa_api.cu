@@ -313,6 +313,53 @@ int make_scan(const qa_model* m, const ScanIn& in, qa::Scan* sc) {
   return QA_OK;
 }
 
+// Brute force (Table I): every state of the box (open) or every composition
+// of N_hat (closed), FP64, one warp per pixel.
+int run_brute(qa_model* m, const qa_raster* r, int closed, int bound, int8_t* out_n,
+              double* out_U, uint8_t* out_flags, void* stream) {
+  if (!m) return fail(QA_ERR_INVALID, "null model");
+  if (!r) return fail(QA_ERR_INVALID, "null raster");
+  if (bound < 0 || bound > 127)
+    return fail(QA_ERR_RANGE, "%s=%d outside [0, 127]", closed ? "n_charges" : "n_max", bound);
+  ScanIn in;
+  in.r = r;
+  qa::Scan sc;
+  int rc = make_scan(m, in, &sc);
+  if (rc) return rc;
+  if (!out_n) return fail(QA_ERR_INVALID, "null out_n");
+  const int R = bound + 1;
+  const int nfree = closed ? m->n - 1 : m->n;
+  double states = 1.0;
+  for (int j = 0; j < nfree; ++j) states *= (double)R;
+  if (states > 1099511627776.0)  // 2^40 per pixel
+    return fail(QA_ERR_RANGE, "%d^%d brute-force states per pixel is too many", R, nfree);
+  int ni = 0;
+  double outer = states;
+  while (ni < nfree && outer / R >= 32.0) { outer /= R; ++ni; }
+  if ((rc = select_device(m))) return rc;
+  qa::BruteLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.a.md = m->d_md;
+  L.a.n = m->n;
+  L.a.ng = m->ng;
+  L.a.sc = sc;
+  L.a.mt.t = 1.0;
+  L.a.mt.closed = closed ? 1 : 0;
+  L.a.mt.n_charges = closed ? bound : 0;
+  L.a.mt.carrier = m->carrier;
+  L.a.out_n = out_n;
+  L.a.out_U = out_U;
+  L.a.out_flags = out_flags;
+  L.radix = R;
+  L.nfree = nfree;
+  L.ni = ni;
+  L.n_max = closed ? -1 : bound;
+  L.nouter = (unsigned long long)(outer + 0.5);
+  cudaError_t e = qa::launch_brute(L, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "brute-force launch");
+  return QA_OK;
+}
+
 int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
                      int n_charges, int8_t* out_n, double* out_U,
                      uint8_t* out_flags, void* stream) {
@@ -613,6 +660,16 @@ int qa_ground_state_points(qa_model* m, const double* V_dev, long long P,
   in.P = P;
   return run_ground_state(m, in, threshold, closed ? 1 : 0, n_charges, out_n, out_U,
                           out_flags, stream);
+}
+
+int qa_brute_force_open(qa_model* m, const qa_raster* r, int n_max, int8_t* out_n,
+                        double* out_U, uint8_t* out_flags, void* stream) {
+  return run_brute(m, r, 0, n_max, out_n, out_U, out_flags, stream);
+}
+
+int qa_brute_force_closed(qa_model* m, const qa_raster* r, int n_charges, int8_t* out_n,
+                          double* out_U, uint8_t* out_flags, void* stream) {
+  return run_brute(m, r, 1, n_charges, out_n, out_U, out_flags, stream);
 }
 
 int qa_soft_occupation(qa_model* m, const qa_raster* r, double kT,

@@ -59,6 +59,19 @@ struct GsLaunch {
   cudaEvent_t* ev;     // optional: events around prep / search / resolve+recheck
 };
 
+// Brute-force ground state (Table I): digit range R, free digits (N open,
+// N - 1 closed), trailing digits walked per outer state, outer states.
+struct BruteLaunch {
+  ArrayDesc a;                 // model, voltages, method (closed, N_hat), outputs
+  int radix;                   // n_max + 1 (open) or N_hat + 1 (closed)
+  int nfree;
+  int ni;
+  int n_max;                   // open: box bound reported by kBruteAtBox
+  unsigned long long nouter;   // radix^(nfree - ni)
+};
+enum : unsigned { kBruteNearTie = 1u, kBruteAtBox = 2u, kBruteNone = 4u };
+cudaError_t launch_brute(const BruteLaunch& L, cudaStream_t st);
+
 // prep -> search -> resolve -> FP64 recheck of one array, enqueued on `st`.
 cudaError_t launch_ground_state(const GsLaunch& a, cudaStream_t st);
 // The same for a batch (persistent kernels over the work queues).

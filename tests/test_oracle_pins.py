@@ -502,3 +502,18 @@ def test_threshold_test_is_inclusive():
     out = oracle.ground_state(cfg["Cdd"], cfg["Cgd"], raster=cfg["raster"], t=1.0)
     assert out["qp_used"].sum() > 0
     assert (out["n_cand"] == 4).all()
+
+
+def test_brute_force_second_energy_single_dot():
+    # one dot, M = 1/C: U(n) = (n - c)^2 / (2C); c = 0.3 -> n = 0 best, n = 1 next
+    C = 2.0
+    M = np.array([[1.0 / C]])
+    bn, bU, hit, visited = oracle.brute_force(M, np.array([0.3]), n_max=4)
+    assert bn.tolist() == [0] and visited == 5 and not hit
+    r = oracle.brute_force_raster(np.array([[C]]), np.array([[1.0]]),
+                                  {"V0": np.zeros(1), "u": np.ones(1), "w": np.zeros(1),
+                                   "x0": 0.3, "x1": 2.8, "y0": 0.0, "y1": 0.0, "W": 2, "H": 1},
+                                  n_max=4)
+    np.testing.assert_array_equal(r["n"][:, 0], [0, 3])
+    np.testing.assert_allclose(r["U"], [0.09 / 4, 0.04 / 4], rtol=1e-14)
+    np.testing.assert_allclose(r["U2"], [0.49 / 4, 0.64 / 4], rtol=1e-14)
