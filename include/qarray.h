@@ -180,6 +180,29 @@ int qa_ground_state_points(qa_model* m, const double* V_dev, long long P,
                            int8_t* out_n, double* out_U, uint8_t* out_flags,
                            void* stream);
 
+/* Optimal gate voltages for a charge state (Sec. IV.C, Eq.
+ * "optimal_gate_voltages"; proof in Appendix H): the V that minimises
+ * 1/2 (Q - s Cgd V)^T Cdd^-1 (Q - s Cgd V), i.e. the least-squares problem
+ * min ||R Q - s R Cgd V||_2 with R^T R = Cdd^-1 (Cholesky), solved by the
+ * Moore-Penrose pseudo-inverse: V = s (R Cgd)^+ R Q (minimum-norm V when the
+ * gates outnumber the dots).  HOST arrays: Cdd [n_dot, n_dot] and Cgd
+ * [n_dot, n_gate] row-major in `form` (QA_FORM_*), Q [n_dot] (charges, in
+ * units of e), V [n_gate] output; s = carrier_sign (+1 or -1).  No GPU is
+ * used.  Errors as qa_model_create, QA_ERR_INVALID for null pointers. */
+int qa_optimal_gate_voltages(const double* Cdd, const double* Cgd, int n_dot, int n_gate,
+                             int form, double carrier_sign, const double* Q, double* V);
+
+/* Virtual gate matrix (Sec. IV.C; Appendix I): alpha = (Cdd^-1 Cgd)^+,
+ * HOST output [n_gate, n_dot] row-major.  Column i is the gate-voltage change
+ * that moves the potential of dot i by one unit and leaves the other dots'
+ * potentials unchanged (exactly when Cdd^-1 Cgd has full row rank; the
+ * least-squares best otherwise); it is the raster direction u or w of a
+ * virtual-gate sweep.  Pseudo-inverse by one-sided Jacobi SVD, singular
+ * values below max(n_dot, n_gate) eps s_max treated as zero.  No GPU is
+ * used. */
+int qa_virtual_gate_matrix(const double* Cdd, const double* Cgd, int n_dot, int n_gate,
+                           int form, double* alpha);
+
 /* Brute-force ground state (Table I, brute-force row; the reference the
  * default and thresholded methods are measured against in Sec. VII, Fig. 4):
  * the exact argmin of U over every n in [0, n_max]^n_dot, in FP64, ties to

@@ -327,3 +327,16 @@ def brute_force_raster(Cdd, Cgd, raster, closed=False, n_charges=0, n_max=3, car
         res["U2"][p] = U2.value
         res["hit"][p] = bool(hit.value)
     return res
+
+
+def optimal_gate_voltages(Cdd, Cgd, Q, carrier=1.0):
+    """Sec. IV.C, Eq. "optimal_gate_voltages" (Appendix H): V* = s (R Cgd)^+ R Q
+    with R^T R = Cdd^-1, from numpy's Cholesky factor and pseudo-inverse."""
+    M = inverse_spd(Cdd)
+    R = np.linalg.cholesky(M).T
+    return carrier * (np.linalg.pinv(R @ np.asarray(Cgd, dtype=np.float64)) @ (R @ np.asarray(Q, dtype=np.float64)))
+
+
+def virtual_gate_matrix(Cdd, Cgd):
+    """Sec. IV.C (Appendix I): alpha = (Cdd^-1 Cgd)^+, [n_gate, n_dot]."""
+    return np.linalg.pinv(inverse_spd(Cdd) @ np.asarray(Cgd, dtype=np.float64))

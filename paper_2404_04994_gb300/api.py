@@ -105,6 +105,8 @@ def load():
                                        I, P, P, P, P]),
         "qa_ground_state_points": (I, [P, P, ctypes.c_longlong, ctypes.c_double, I, I,
                                        P, P, P, P]),
+        "qa_optimal_gate_voltages": (I, [P, P, I, I, I, ctypes.c_double, P, P]),
+        "qa_virtual_gate_matrix": (I, [P, P, I, I, I, P]),
         "qa_brute_force_open": (I, [P, ctypes.POINTER(qa_raster), I, P, P, P, P]),
         "qa_brute_force_closed": (I, [P, ctypes.POINTER(qa_raster), I, P, P, P, P]),
         "qa_soft_occupation": (I, [P, ctypes.POINTER(qa_raster), ctypes.c_double,
@@ -297,6 +299,47 @@ def qa_ground_state_points(m, V, threshold, closed, n_charges, out_n, out_U=None
 
 BF_NEAR_TIE = 1
 BF_AT_BOX = 2
+
+
+def _host(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def qa_optimal_gate_voltages(Cdd, Cgd, Q, form=QA_FORM_MAXWELL, carrier_sign=1.0):
+    """Gate voltages minimising the free energy of charge state Q (host)."""
+    Cgd = np.ascontiguousarray(Cgd, dtype=np.float64)
+    n, ng = Cgd.shape
+    Cdd = _host(Cdd, (n, n))
+    Q = _host(Q, (n,))
+    V = np.zeros(ng)
+    _check(load().qa_optimal_gate_voltages(
+        Cdd.ctypes.data, Cgd.ctypes.data, n, ng, int(form), float(carrier_sign),
+        Q.ctypes.data, V.ctypes.data))
+    return V
+
+
+def qa_virtual_gate_matrix(Cdd, Cgd, form=QA_FORM_MAXWELL):
+    """alpha = (Cdd^-1 Cgd)^+, [n_gate, n_dot] (host)."""
+    Cgd = np.ascontiguousarray(Cgd, dtype=np.float64)
+    n, ng = Cgd.shape
+    Cdd = _host(Cdd, (n, n))
+    alpha = np.zeros((ng, n))
+    _check(load().qa_virtual_gate_matrix(Cdd.ctypes.data, Cgd.ctypes.data, n, ng, int(form),
+                                         alpha.ctypes.data))
+    return alpha
+
+
+def virtual_raster(Cdd, Cgd, V0, dot_x, dot_y, lo=-1.0, hi=1.0, W=100, H=100,
+                   form=QA_FORM_MAXWELL):
+    """Raster sweeping the virtual gates of dots dot_x (fast axis) and dot_y
+    around the gate voltages V0: u, w are columns of the virtual gate matrix."""
+    alpha = qa_virtual_gate_matrix(Cdd, Cgd, form)
+    return {"V0": np.asarray(V0, dtype=np.float64), "u": alpha[:, dot_x].copy(),
+            "w": alpha[:, dot_y].copy(), "x0": lo, "x1": hi, "y0": lo, "y1": hi,
+            "W": int(W), "H": int(H)}
 
 
 def qa_brute_force_open(m, raster, n_max, out_n, out_U=None, out_flags=None, stream=None):

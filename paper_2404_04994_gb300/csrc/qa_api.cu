@@ -4,6 +4,7 @@
 // Appendix B positive-definiteness check), workspace management and kernel
 // dispatch.  No pixel work happens on the host.
 #include <algorithm>
+#include <memory>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -193,6 +194,66 @@ int build_model(int n, int ng, int form, const double* Cdd_in,
   md->status = 0;
   fill_consts(n, md);
   return QA_OK;
+}
+
+// Moore-Penrose pseudo-inverse of the m x k row-major A into the k x m
+// row-major P, by one-sided Jacobi SVD (Hestenes 1958): plane rotations of
+// the columns of W = A (accumulated in V) until every pair is orthogonal to
+// working precision; then W = U S, A = U S V^T and
+//     A^+ = sum_{s_j > tol} V e_j (W e_j)^T / s_j^2,
+// with tol = max(m, k) eps max_j s_j (singular values below are treated as
+// zero).  Host FP64; m, k <= 64.
+void pinv(int m, int k, const double* A, double* P) {
+  std::vector<double> W((size_t)m * k), V((size_t)k * k, 0.0);
+  for (int e = 0; e < m * k; ++e) W[(size_t)e] = A[e];
+  for (int j = 0; j < k; ++j) V[(size_t)j * k + j] = 1.0;
+  const double eps = 2.220446049250313e-16;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    bool rotated = false;
+    for (int p = 0; p < k - 1; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        double a = 0.0, b = 0.0, c = 0.0;
+        for (int i = 0; i < m; ++i) {
+          const double wp = W[(size_t)i * k + p], wq = W[(size_t)i * k + q];
+          a += wp * wp;
+          b += wq * wq;
+          c += wp * wq;
+        }
+        if (c == 0.0 || std::fabs(c) <= eps * std::sqrt(a * b)) continue;
+        rotated = true;
+        const double zeta = (b - a) / (2.0 * c);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = cs * t;
+        for (int i = 0; i < m; ++i) {
+          const double wp = W[(size_t)i * k + p], wq = W[(size_t)i * k + q];
+          W[(size_t)i * k + p] = cs * wp - sn * wq;
+          W[(size_t)i * k + q] = sn * wp + cs * wq;
+        }
+        for (int i = 0; i < k; ++i) {
+          const double vp = V[(size_t)i * k + p], vq = V[(size_t)i * k + q];
+          V[(size_t)i * k + p] = cs * vp - sn * vq;
+          V[(size_t)i * k + q] = sn * vp + cs * vq;
+        }
+      }
+    if (!rotated) break;
+  }
+  std::vector<double> s2((size_t)k, 0.0);
+  double smax = 0.0;
+  for (int j = 0; j < k; ++j) {
+    double a = 0.0;
+    for (int i = 0; i < m; ++i) a += W[(size_t)i * k + j] * W[(size_t)i * k + j];
+    s2[(size_t)j] = a;
+    smax = std::fmax(smax, std::sqrt(a));
+  }
+  const double tol = (double)std::max(m, k) * eps * smax;
+  for (int e = 0; e < k * m; ++e) P[e] = 0.0;
+  for (int j = 0; j < k; ++j) {
+    if (!(std::sqrt(s2[(size_t)j]) > tol)) continue;
+    for (int r = 0; r < k; ++r) {
+      const double vr = V[(size_t)r * k + j] / s2[(size_t)j];
+      for (int i = 0; i < m; ++i) P[(size_t)r * m + i] += vr * W[(size_t)i * k + j];
+    }
+  }
 }
 
 int ensure_workspace(qa_model* m, size_t bytes) {
@@ -660,6 +721,61 @@ int qa_ground_state_points(qa_model* m, const double* V_dev, long long P,
   in.P = P;
   return run_ground_state(m, in, threshold, closed ? 1 : 0, n_charges, out_n, out_U,
                           out_flags, stream);
+}
+
+int qa_optimal_gate_voltages(const double* Cdd, const double* Cgd, int n_dot, int n_gate,
+                             int form, double carrier_sign, const double* Q, double* V) {
+  if (!Q || !V) return fail(QA_ERR_INVALID, "null Q or V");
+  if (!(carrier_sign == 1.0 || carrier_sign == -1.0))
+    return fail(QA_ERR_INVALID, "carrier_sign must be +1 or -1");
+  std::unique_ptr<qa::ModelData> md(new qa::ModelData());
+  int rc = build_model(n_dot, n_gate, form, Cdd, Cgd, md.get());
+  if (rc) return rc;
+  const int n = n_dot, ng = n_gate;
+  // R upper triangular with R^T R = M: R^T is the Cholesky factor of M
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double d = md->M[j * n + j];
+    for (int q = 0; q < j; ++q) d -= L[(size_t)j * n + q] * L[(size_t)j * n + q];
+    if (!(d > 0.0)) return fail(QA_ERR_NOT_PD, "Cdd^-1 is not positive definite");
+    const double ljj = std::sqrt(d);
+    L[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double e = md->M[i * n + j];
+      for (int q = 0; q < j; ++q) e -= L[(size_t)i * n + q] * L[(size_t)j * n + q];
+      L[(size_t)i * n + j] = e / ljj;
+    }
+  }
+  std::vector<double> A((size_t)n * ng, 0.0), b((size_t)n, 0.0), P((size_t)ng * n);
+  for (int i = 0; i < n; ++i) {   // (R A)_ig = sum_j L_ji Cgd_jg, (R Q)_i = sum_j L_ji Q_j
+    for (int j = i; j < n; ++j) {
+      const double rij = L[(size_t)j * n + i];
+      for (int g = 0; g < ng; ++g) A[(size_t)i * ng + g] += rij * md->Cgd[j * ng + g];
+      b[(size_t)i] += rij * Q[j];
+    }
+  }
+  pinv(n, ng, A.data(), P.data());
+  for (int g = 0; g < ng; ++g) {
+    double v = 0.0;
+    for (int i = 0; i < n; ++i) v += P[(size_t)g * n + i] * b[(size_t)i];
+    V[g] = carrier_sign * v;
+  }
+  return QA_OK;
+}
+
+int qa_virtual_gate_matrix(const double* Cdd, const double* Cgd, int n_dot, int n_gate,
+                           int form, double* alpha) {
+  if (!alpha) return fail(QA_ERR_INVALID, "null alpha");
+  std::unique_ptr<qa::ModelData> md(new qa::ModelData());
+  int rc = build_model(n_dot, n_gate, form, Cdd, Cgd, md.get());
+  if (rc) return rc;
+  const int n = n_dot, ng = n_gate;
+  std::vector<double> A((size_t)n * ng, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int g = 0; g < ng; ++g) A[(size_t)i * ng + g] += md->M[i * n + j] * md->Cgd[j * ng + g];
+  pinv(n, ng, A.data(), alpha);
+  return QA_OK;
 }
 
 int qa_brute_force_open(qa_model* m, const qa_raster* r, int n_max, int8_t* out_n,

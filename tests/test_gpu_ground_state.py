@@ -188,3 +188,14 @@ def test_errors_are_reported(qa):
         m.ground_state_closed(cfg["raster"], -1)
     assert e.value.code == -5
     m.close()
+
+
+def test_virtual_gate_raster(qa):
+    # a sweep along the virtual gates of dots 1 and 2 (Sec. IV.C): u, w are
+    # columns of (Cdd^-1 Cgd)^+; the map matches the oracle on that raster
+    cfg = inputs.chain4()
+    ras = qa.virtual_raster(cfg["Cdd"], cfg["Cgd"], np.full(4, 2.0), 1, 2, lo=-3.0, hi=3.0,
+                            W=37, H=29)
+    n, U, f, st = _gpu(qa, cfg, raster=ras, closed=False)
+    rep = compare(n, U, f, _oracle(cfg, raster=ras, closed=False), cfg["Cdd"], "virtual raster")
+    assert rep["comparable"] > 0.95 * 37 * 29
