@@ -301,19 +301,14 @@ BF_NEAR_TIE = 1
 BF_AT_BOX = 2
 
 
-def _host(a, shape):
-    a = np.ascontiguousarray(a, dtype=np.float64)
-    if a.shape != shape:
-        raise ValueError(f"expected shape {shape}, got {a.shape}")
-    return a
 
 
 def qa_optimal_gate_voltages(Cdd, Cgd, Q, form=QA_FORM_MAXWELL, carrier_sign=1.0):
     """Gate voltages minimising the free energy of charge state Q (host)."""
     Cgd = np.ascontiguousarray(Cgd, dtype=np.float64)
     n, ng = Cgd.shape
-    Cdd = _host(Cdd, (n, n))
-    Q = _host(Q, (n,))
+    Cdd, _ = _host(Cdd, (n, n))
+    Q, _ = _host(Q, (n,))
     V = np.zeros(ng)
     _check(load().qa_optimal_gate_voltages(
         Cdd.ctypes.data, Cgd.ctypes.data, n, ng, int(form), float(carrier_sign),
@@ -325,7 +320,7 @@ def qa_virtual_gate_matrix(Cdd, Cgd, form=QA_FORM_MAXWELL):
     """alpha = (Cdd^-1 Cgd)^+, [n_gate, n_dot] (host)."""
     Cgd = np.ascontiguousarray(Cgd, dtype=np.float64)
     n, ng = Cgd.shape
-    Cdd = _host(Cdd, (n, n))
+    Cdd, _ = _host(Cdd, (n, n))
     alpha = np.zeros((ng, n))
     _check(load().qa_virtual_gate_matrix(Cdd.ctypes.data, Cgd.ctypes.data, n, ng, int(form),
                                          alpha.ctypes.data))
