@@ -203,6 +203,45 @@ int qa_optimal_gate_voltages(const double* Cdd, const double* Cgd, int n_dot, in
 int qa_virtual_gate_matrix(const double* Cdd, const double* Cgd, int n_dot, int n_gate,
                            int form, double* alpha);
 
+/* Charge-sensor response (Sec. IV.A).  `m` is the FULL system: its last
+ * n_sensor dots are the sensing dots (1 <= n_sensor <= 4, fewer than n_dot).
+ * n_dots (DEVICE int8 [H, W, n_dot - n_sensor]) is the ground state of the
+ * other dots, computed by the caller without the sensors but with every gate
+ * (so the sensor gates' cross-talk is included), e.g. by
+ * qa_ground_state_open/closed on the model made of the leading blocks of Cdd
+ * and Cgd.  Per pixel, with those charges fixed:
+ *   1. each sensor takes the charge minimising U (floor / floor + 1 around the
+ *      continuous sensor minimum c_S - (M_SS)^-1 M_SD (n_D - c_D); 2^S
+ *      candidates, ties to the lexicographically smaller);
+ *   2. its potential V_s = (M (n - c))_s (Eq. "potential");
+ *   3. the response at detuning eps = M_ss / 2 - |V_s| from the nearest
+ *      Coulomb peak: 1 / (1 + (eps / width)^2) (QA_SENSOR_LORENTZIAN, weak
+ *      coupling) or exp(-eps^2 / (2 width^2)) (QA_SENSOR_GAUSSIAN, strong);
+ *   4. plus noise along each raster row: white (white_sigma), 1/f
+ *      (pink_sigma; Voss-McCartney octaves) and a random telegraph of
+ *      jump_amplitude switching with probability jump_prob per pixel; all
+ *      drawn from Philox4x32-10 keyed by `seed`, so a result depends only on
+ *      the inputs.
+ * DEVICE outputs, caller-owned: out_signal float [H, W, n_sensor];
+ * out_n_sensor int8 and out_potential FP64 [H, W, n_sensor] (nullable).
+ * W <= 8192.  FP64 arithmetic.  Errors: QA_ERR_INVALID, QA_ERR_RANGE,
+ * QA_ERR_SHAPE, QA_ERR_CUDA. */
+#define QA_SENSOR_LORENTZIAN 0
+#define QA_SENSOR_GAUSSIAN   1
+typedef struct {
+    int n_sensor;
+    int shape;
+    double width;
+    double white_sigma;
+    double pink_sigma;
+    double jump_amplitude;
+    double jump_prob;
+    unsigned long long seed;
+} qa_sensor_params;
+int qa_charge_sensor(qa_model* m, const qa_raster* r, const int8_t* n_dots,
+                     const qa_sensor_params* sp, float* out_signal, int8_t* out_n_sensor,
+                     double* out_potential, void* stream);
+
 /* Brute-force ground state (Table I, brute-force row; the reference the
  * default and thresholded methods are measured against in Sec. VII, Fig. 4):
  * the exact argmin of U over every n in [0, n_max]^n_dot, in FP64, ties to

@@ -112,6 +112,9 @@ def _load():
                                      D, ctypes.c_int, D, D, D]
         lib.qo_raster_c.argtypes = [ctypes.c_int, ctypes.c_int, D,
                                     ctypes.c_double, R, ctypes.c_long, D]
+        lib.qo_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint)] * 3
+        lib.qo_charge_sensor.argtypes = [ctypes.c_int, ctypes.c_int, D, D, ctypes.c_double, R,
+                                         I, ctypes.c_void_p, D, I, D]
         lib.qo_brute_force.argtypes = [ctypes.c_int, D, D, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int, I, D, I]
         lib.qo_brute_force.restype = ctypes.c_long
@@ -340,3 +343,46 @@ def optimal_gate_voltages(Cdd, Cgd, Q, carrier=1.0):
 def virtual_gate_matrix(Cdd, Cgd):
     """Sec. IV.C (Appendix I): alpha = (Cdd^-1 Cgd)^+, [n_gate, n_dot]."""
     return np.linalg.pinv(inverse_spd(Cdd) @ np.asarray(Cgd, dtype=np.float64))
+
+
+class _SensorParams(ctypes.Structure):
+    _fields_ = [("n_sensor", ctypes.c_int), ("shape", ctypes.c_int),
+                ("width", ctypes.c_double), ("white_sigma", ctypes.c_double),
+                ("pink_sigma", ctypes.c_double), ("jump_amplitude", ctypes.c_double),
+                ("jump_prob", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of four 32-bit counter words and two key words."""
+    c = (ctypes.c_uint * 4)(*[int(v) & 0xffffffff for v in ctr])
+    k = (ctypes.c_uint * 2)(*[int(v) & 0xffffffff for v in key])
+    o = (ctypes.c_uint * 4)()
+    _load().qo_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def charge_sensor(Cdd_full, Cgd_full, raster, n_dots, n_sensor=1, shape=0, width=0.05,
+                  white_sigma=0.0, pink_sigma=0.0, jump_amplitude=0.0, jump_prob=0.0,
+                  seed=0, carrier=1.0):
+    """Sec. IV.A sensor response given the dots' ground state n_dots
+    [P, n_full - n_sensor]: dict of signal, n_sensor, potential, each [P, S]."""
+    Cdd_full, pC = _d(Cdd_full)
+    Cgd_full, pG = _d(Cgd_full)
+    nf, ng = Cgd_full.shape
+    P = int(raster["W"]) * int(raster["H"])
+    nd = np.ascontiguousarray(np.asarray(n_dots).reshape(P, nf - n_sensor), dtype=np.int32)
+    sp = _SensorParams(int(n_sensor), int(shape), float(width), float(white_sigma),
+                       float(pink_sigma), float(jump_amplitude), float(jump_prob), int(seed))
+    sig = np.zeros((P, n_sensor))
+    ns = np.zeros((P, n_sensor), dtype=np.int32)
+    pot = np.zeros((P, n_sensor))
+    rs = _raster(raster)
+    st = _load().qo_charge_sensor(nf, ng, pC, pG, float(carrier), ctypes.byref(rs),
+                                  nd.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                  ctypes.byref(sp),
+                                  sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                  pot.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if st != 0:
+        raise ValueError("oracle charge sensor: bad input")
+    return {"signal": sig, "n_sensor": ns, "potential": pot}

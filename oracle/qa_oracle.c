@@ -694,3 +694,162 @@ long qo_brute_force2(int n, const double* M, const double* c, int closed,
             if (out_n[i] == n_max) *hit_nmax = 1;
     return count;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Charge sensors (Sec. IV.A)                                               */
+/* ------------------------------------------------------------------------ */
+
+void qo_philox4x32_10(const unsigned* ctr, const unsigned* key, unsigned* out)
+{
+    unsigned c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    unsigned k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+        unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+        unsigned n0 = (unsigned)(p1 >> 32) ^ c1 ^ k0;
+        unsigned n1 = (unsigned)p1;
+        unsigned n2 = (unsigned)(p0 >> 32) ^ c3 ^ k1;
+        unsigned n3 = (unsigned)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static void sensor_draw(unsigned long long seed, unsigned tag, unsigned row,
+                        unsigned idx, unsigned* out)
+{
+    unsigned ctr[4] = {tag, row, idx, 0u};
+    unsigned key[2] = {(unsigned)seed, (unsigned)(seed >> 32)};
+    qo_philox4x32_10(ctr, key, out);
+}
+
+static double sensor_normal(unsigned long long seed, unsigned tag, unsigned row,
+                            unsigned idx)
+{
+    unsigned x[4];
+    sensor_draw(seed, tag, row, idx, x);
+    double u1 = ((double)x[0] + 1.0) / 4294967296.0;
+    double u2 = (double)x[1] / 4294967296.0;
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * 3.14159265358979323846 * u2);
+}
+
+/* telegraph state (0/1) at every index < len of one row */
+static void sensor_telegraph(unsigned long long seed, unsigned tag, unsigned row,
+                             double prob, int len, unsigned char* state)
+{
+    for (int i = 0; i < len; ++i) state[i] = 0;
+    if (!(prob > 0.0)) return;
+    long pos = -1;
+    unsigned j = 0;
+    for (;;) {
+        unsigned x[4];
+        sensor_draw(seed, tag, row, j++, x);
+        double u = ((double)x[0] + 1.0) / 4294967296.0;
+        double g = prob >= 1.0 ? 1.0 : 1.0 + floor(log(u) / log(1.0 - prob));
+        if (g > (double)len) break;
+        pos += (long)g;
+        if (pos >= len) break;
+        for (long i = pos; i < len; ++i) state[i] ^= 1u;
+    }
+}
+
+int qo_charge_sensor(int n_full, int n_gate, const double* Cdd_full,
+                     const double* Cgd_full, double carrier, const qo_raster* r,
+                     const int* n_dots, const qo_sensor_params* sp,
+                     double* signal, int* n_sensor, double* potential)
+{
+    int S = sp->n_sensor, nd = n_full - S;
+    if (S < 1 || S > 4 || nd < 1 || n_full > N || !(sp->width > 0.0)) return -1;
+    if (!(sp->jump_prob >= 0.0 && sp->jump_prob < 1.0)) return -1;
+    double M[N * N];
+    if (qo_inverse_spd(n_full, Cdd_full, M)) return -1;
+    /* (M_SS)^-1 */
+    double Mss[16], Mssi[16];
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; b < S; ++b) Mss[a * S + b] = M[(nd + a) * n_full + nd + b];
+    if (qo_inverse_spd(S, Mss, Mssi)) return -1;
+    int K = 1;
+    while ((1 << (K - 1)) < r->W) ++K;
+    unsigned char* tel = (unsigned char*)malloc((size_t)r->W);
+    long P = (long)r->W * r->H;
+    for (int s = 0; s < S; ++s) {
+        for (int row = 0; row < r->H; ++row) {
+            sensor_telegraph(sp->seed, 2u | ((unsigned)s << 4), (unsigned)row, sp->jump_prob,
+                             r->W, tel);
+            for (int col = 0; col < r->W; ++col) {
+                long p = (long)row * r->W + col;
+                /* computed per sensor from scratch: steps 1-2 */
+                double c[N];
+                pixel_c(n_full, n_gate, Cgd_full, carrier, r, NULL, p, c);
+                int nv[N];
+                for (int i = 0; i < nd; ++i) nv[i] = n_dots[p * nd + i];
+                double g[4], xs[4];
+                for (int a = 0; a < S; ++a) {
+                    double acc = 0.0;
+                    for (int j = 0; j < nd; ++j)
+                        acc += M[(nd + a) * n_full + j] * ((double)nv[j] - c[j]);
+                    g[a] = acc;
+                }
+                for (int a = 0; a < S; ++a) {
+                    double acc = 0.0;
+                    for (int b = 0; b < S; ++b) acc += Mssi[a * S + b] * g[b];
+                    xs[a] = c[nd + a] - acc;
+                }
+                int best[4] = {0, 0, 0, 0}, have = 0;
+                double bestU = 0.0;
+                for (int m = 0; m < (1 << S); ++m) {
+                    int cand[N];
+                    for (int i = 0; i < nd; ++i) cand[i] = nv[i];
+                    for (int a = 0; a < S; ++a) {
+                        double xa = xs[a] > 0.0 ? xs[a] : 0.0;
+                        cand[nd + a] = (int)floor(xa) + ((m >> a) & 1);
+                    }
+                    double U = qo_energy(n_full, M, cand, c);
+                    int better = !have || U < bestU;
+                    if (have && U == bestU) {
+                        int lt = 0;
+                        for (int a = 0; a < S; ++a)
+                            if (cand[nd + a] != best[a]) { lt = cand[nd + a] < best[a]; break; }
+                        better = lt;
+                    }
+                    if (better) {
+                        have = 1;
+                        bestU = U;
+                        for (int a = 0; a < S; ++a) best[a] = cand[nd + a];
+                    }
+                }
+                for (int a = 0; a < S; ++a) nv[nd + a] = best[a];
+                /* step 2: potential of sensor s */
+                int q = nd + s;
+                double V = 0.0;
+                for (int j = 0; j < n_full; ++j) V += M[q * n_full + j] * ((double)nv[j] - c[j]);
+                /* step 3: line shape */
+                double eps = 0.5 * M[q * n_full + q] - fabs(V);
+                double y = eps / sp->width;
+                double resp = sp->shape == 1 ? exp(-0.5 * y * y) : 1.0 / (1.0 + y * y);
+                /* step 4: noise */
+                double noise = 0.0;
+                if (sp->white_sigma > 0.0)
+                    noise += sp->white_sigma *
+                             sensor_normal(sp->seed, 0u | ((unsigned)s << 4), (unsigned)row, (unsigned)col);
+                if (sp->pink_sigma > 0.0) {
+                    double acc = 0.0;
+                    for (int k = 0; k < K; ++k)
+                        acc += sensor_normal(sp->seed, 1u | ((unsigned)s << 4) | ((unsigned)k << 8),
+                                             (unsigned)row, (unsigned)col >> k);
+                    noise += sp->pink_sigma * acc / sqrt((double)K);
+                }
+                if (tel[col]) noise += sp->jump_amplitude;
+                signal[p * S + s] = resp + noise;
+                n_sensor[p * S + s] = nv[q];
+                potential[p * S + s] = V;
+            }
+        }
+    }
+    free(tel);
+    return 0;
+}

@@ -121,6 +121,46 @@ long qo_brute_force2(int n, const double* M, const double* c, int closed,
                      int n_charges, int n_max, int* out_n, double* out_U,
                      double* out_U2, int* hit_nmax);
 
+/* ------------------------------------------------------------------------ */
+/* Charge sensors (Sec. IV.A)                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11): ten rounds of the
+ * published round function (multipliers 0xD2511F53 and 0xCD9E8D57, key
+ * schedule bumped by 0x9E3779B9 and 0xBB67AE85 between rounds). */
+void qo_philox4x32_10(const unsigned* ctr, const unsigned* key, unsigned* out);
+
+typedef struct {
+    int n_sensor;             /* the last n_sensor dots of the model        */
+    int shape;                /* 0 Lorentzian, 1 Gaussian                   */
+    double width;             /* gamma > 0                                  */
+    double white_sigma, pink_sigma, jump_amplitude, jump_prob;
+    unsigned long long seed;
+} qo_sensor_params;
+
+/* Sensor response on every pixel of a raster (Sec. IV.A), given the dots'
+ * ground state n_dots [P, n_full - S] (int):
+ *   1. with the dots fixed, each sensor takes the charge minimising the full
+ *      energy U: the best of the floor / floor + 1 values around the
+ *      continuous sensor minimum x_S = c_S - (M_SS)^-1 M_SD (n_D - c_D)
+ *      (2^S candidates, direct energies, lexicographic ties);
+ *   2. the sensor potential V_S = (M (n - c))_S (Eq. "potential");
+ *   3. the distance to the nearest Coulomb peak eps = M_ss / 2 - |V_s| and
+ *      the line shape 1 / (1 + (eps / gamma)^2) or exp(-eps^2 / (2 gamma^2));
+ *   4. noise: white (one normal deviate per pixel), 1/f along the fast axis
+ *      (Voss-McCartney: octave k redrawn every 2^k pixels, K octaves with
+ *      2^(K-1) >= W, sum / sqrt(K)) and a random telegraph of amplitude
+ *      jump_amplitude switching with probability jump_prob per pixel
+ *      (geometric gaps), all drawn from Philox4x32-10 with key = seed and
+ *      counter (kind | sensor << 4 | octave << 8, row, index, 0); normals by
+ *      Box-Muller from u1 = (x0 + 1) / 2^32, u2 = x1 / 2^32.
+ * Outputs [P, S]: signal, sensor charges, potentials.  Returns 0, or -1 on
+ * bad input. */
+int qo_charge_sensor(int n_full, int n_gate, const double* Cdd_full,
+                     const double* Cgd_full, double carrier, const qo_raster* r,
+                     const int* n_dots, const qo_sensor_params* sp,
+                     double* signal, int* n_sensor, double* potential);
+
 #ifdef __cplusplus
 }
 #endif

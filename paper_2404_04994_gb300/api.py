@@ -64,6 +64,17 @@ class qa_stats(ctypes.Structure):
         ("ms_recheck", ctypes.c_double), ("ms_soft", ctypes.c_double)]
 
 
+class qa_sensor_params(ctypes.Structure):
+    _fields_ = [("n_sensor", ctypes.c_int), ("shape", ctypes.c_int),
+                ("width", ctypes.c_double), ("white_sigma", ctypes.c_double),
+                ("pink_sigma", ctypes.c_double), ("jump_amplitude", ctypes.c_double),
+                ("jump_prob", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+
+
+QA_SENSOR_LORENTZIAN = 0
+QA_SENSOR_GAUSSIAN = 1
+
+
 class qa_batch_item(ctypes.Structure):
     _fields_ = [("model", ctypes.c_void_p), ("raster", qa_raster),
                 ("threshold", ctypes.c_double), ("closed", ctypes.c_int),
@@ -107,6 +118,8 @@ def load():
                                        P, P, P, P]),
         "qa_optimal_gate_voltages": (I, [P, P, I, I, I, ctypes.c_double, P, P]),
         "qa_virtual_gate_matrix": (I, [P, P, I, I, I, P]),
+        "qa_charge_sensor": (I, [P, ctypes.POINTER(qa_raster), P,
+                                 ctypes.POINTER(qa_sensor_params), P, P, P, P]),
         "qa_brute_force_open": (I, [P, ctypes.POINTER(qa_raster), I, P, P, P, P]),
         "qa_brute_force_closed": (I, [P, ctypes.POINTER(qa_raster), I, P, P, P, P]),
         "qa_soft_occupation": (I, [P, ctypes.POINTER(qa_raster), ctypes.c_double,
@@ -299,6 +312,27 @@ def qa_ground_state_points(m, V, threshold, closed, n_charges, out_n, out_U=None
 
 BF_NEAR_TIE = 1
 BF_AT_BOX = 2
+
+
+def qa_charge_sensor(m, raster, n_dots, params, out_signal, out_n_sensor=None,
+                     out_potential=None, stream=None):
+    """params: dict with n_sensor, shape, width, white_sigma, pink_sigma,
+    jump_amplitude, jump_prob, seed."""
+    import torch
+    n, ng = qa_model_shape(m)
+    r = make_raster(raster, ng)
+    P = r.W * r.H
+    S = int(params["n_sensor"])
+    sp = qa_sensor_params(S, int(params.get("shape", 0)), float(params.get("width", 0.05)),
+                          float(params.get("white_sigma", 0.0)),
+                          float(params.get("pink_sigma", 0.0)),
+                          float(params.get("jump_amplitude", 0.0)),
+                          float(params.get("jump_prob", 0.0)), int(params.get("seed", 0)))
+    _check(load().qa_charge_sensor(
+        m, ctypes.byref(r), _dev(n_dots, torch.int8, P * (n - S), "n_dots"), ctypes.byref(sp),
+        _dev(out_signal, torch.float32, P * S, "out_signal"),
+        _dev(out_n_sensor, torch.int8, P * S, "out_n_sensor"),
+        _dev(out_potential, torch.float64, P * S, "out_potential"), _stream(stream)))
 
 
 

@@ -778,6 +778,54 @@ int qa_virtual_gate_matrix(const double* Cdd, const double* Cgd, int n_dot, int 
   return QA_OK;
 }
 
+int qa_charge_sensor(qa_model* m, const qa_raster* r, const int8_t* n_dots,
+                     const qa_sensor_params* sp, float* out_signal, int8_t* out_n_sensor,
+                     double* out_potential, void* stream) {
+  if (!m || !r || !sp) return fail(QA_ERR_INVALID, "null argument");
+  if (sp->n_sensor < 1 || sp->n_sensor > 4 || sp->n_sensor >= m->n)
+    return fail(QA_ERR_RANGE, "n_sensor=%d outside [1, min(4, n_dot - 1)]", sp->n_sensor);
+  if (sp->shape != QA_SENSOR_LORENTZIAN && sp->shape != QA_SENSOR_GAUSSIAN)
+    return fail(QA_ERR_INVALID, "unknown sensor shape %d", sp->shape);
+  if (!(sp->width > 0.0) || !(sp->white_sigma >= 0.0) || !(sp->pink_sigma >= 0.0) ||
+      !std::isfinite(sp->width) || !std::isfinite(sp->white_sigma) ||
+      !std::isfinite(sp->pink_sigma) || !std::isfinite(sp->jump_amplitude))
+    return fail(QA_ERR_RANGE, "sensor width must be > 0 and noise levels >= 0");
+  if (!(sp->jump_prob >= 0.0 && sp->jump_prob < 1.0))
+    return fail(QA_ERR_RANGE, "jump_prob %g outside [0, 1)", sp->jump_prob);
+  ScanIn in;
+  in.r = r;
+  qa::Scan sc;
+  int rc = make_scan(m, in, &sc);
+  if (rc) return rc;
+  if (sc.W > 8192) return fail(QA_ERR_SHAPE, "sensor rasters hold at most 8192 columns");
+  if (!n_dots || !out_signal) return fail(QA_ERR_INVALID, "null n_dots or out_signal");
+  if ((rc = select_device(m))) return rc;
+  qa::SensorLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  L.a.md = m->d_md;
+  L.a.n = m->n;
+  L.a.ng = m->ng;
+  L.a.sc = sc;
+  L.a.mt.carrier = m->carrier;
+  L.S = sp->n_sensor;
+  L.shape = sp->shape;
+  L.K = 1;
+  while ((1 << (L.K - 1)) < sc.W) ++L.K;
+  L.width = sp->width;
+  L.white_sigma = sp->white_sigma;
+  L.pink_sigma = sp->pink_sigma;
+  L.jump_amplitude = sp->jump_amplitude;
+  L.jump_prob = sp->jump_prob;
+  L.seed = sp->seed;
+  L.n_dots = n_dots;
+  L.out_signal = out_signal;
+  L.out_n_sensor = out_n_sensor;
+  L.out_potential = out_potential;
+  cudaError_t e = qa::launch_sensor(L, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "sensor launch");
+  return QA_OK;
+}
+
 int qa_brute_force_open(qa_model* m, const qa_raster* r, int n_max, int8_t* out_n,
                         double* out_U, uint8_t* out_flags, void* stream) {
   return run_brute(m, r, 0, n_max, out_n, out_U, out_flags, stream);

@@ -72,6 +72,23 @@ struct BruteLaunch {
 enum : unsigned { kBruteNearTie = 1u, kBruteAtBox = 2u, kBruteNone = 4u };
 cudaError_t launch_brute(const BruteLaunch& L, cudaStream_t st);
 
+// Charge-sensor response (Sec. IV.A) over a raster: the model is the full
+// system, its last S dots the sensors; n_dots holds the other dots' ground
+// state [P, n - S].
+struct SensorLaunch {
+  ArrayDesc a;                 // full model, raster, carrier
+  int S;                       // sensors (1..4)
+  int shape;                   // 0 Lorentzian, 1 Gaussian
+  int K;                       // 1/f octaves: 2^(K-1) >= W
+  double width, white_sigma, pink_sigma, jump_amplitude, jump_prob;
+  unsigned long long seed;
+  const int8_t* n_dots;
+  float* out_signal;           // [P, S]
+  int8_t* out_n_sensor;        // [P, S] (nullable)
+  double* out_potential;       // [P, S] (nullable)
+};
+cudaError_t launch_sensor(const SensorLaunch& L, cudaStream_t st);
+
 // prep -> search -> resolve -> FP64 recheck of one array, enqueued on `st`.
 cudaError_t launch_ground_state(const GsLaunch& a, cudaStream_t st);
 // The same for a batch (persistent kernels over the work queues).
