@@ -47,10 +47,14 @@ template <int L1, int L2>
 __device__ __forceinline__ void search_any(const GsLaunch& L, const ArrayDesc& a,
                                            SearchShared& sh, int array, long long tb,
                                            long long end, SearchAcc& acc) {
-  if (a.mt.closed)
-    search_tile<L1, L2, true>(L, a, sh, array, tb, end, acc);
-  else
-    search_tile<L1, L2, false>(L, a, sh, array, tb, end, acc);
+  const bool tf = a.cfg.T >= kTeamFinishMin;
+  if (a.mt.closed) {
+    if (tf) search_tile<L1, L2, true, true>(L, a, sh, array, tb, end, acc);
+    else search_tile<L1, L2, true, false>(L, a, sh, array, tb, end, acc);
+  } else {
+    if (tf) search_tile<L1, L2, false, true>(L, a, sh, array, tb, end, acc);
+    else search_tile<L1, L2, false, false>(L, a, sh, array, tb, end, acc);
+  }
 }
 
 __global__ void __launch_bounds__(kSearchThreads) k_search_batch(GsLaunch L) {

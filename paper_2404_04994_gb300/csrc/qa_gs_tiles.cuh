@@ -18,6 +18,7 @@ constexpr int kRecheckThreads = 128;
 constexpr int kResolveThreads = 256;
 constexpr int kCheckL1 = 4, kCheckL2 = 3;  // resolve/recheck split: 2^9 outer states at k = 16
 constexpr unsigned kBcap = 1024;
+constexpr int kTeamFinishMin = 8;  // teams at least this wide finish the winning block together
 
 // number of k-subsets of size w (k <= 16)
 __device__ __forceinline__ unsigned long long binom(int k, int w) {
@@ -313,7 +314,7 @@ struct SearchAcc {
 // doubt go on the FP64 recheck list, near ties on the resolve list.  All
 // threads of the block must call.
 // ---------------------------------------------------------------------------
-template <int L1, int L2, bool CLOSED>
+template <int L1, int L2, bool CLOSED, bool TF>
 __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, SearchShared& sh,
                                    int array, long long team_base, long long p_end,
                                    SearchAcc& acc) {
@@ -328,29 +329,44 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
   const PixRec* rec = a.recs + (active ? p : 0);
   const unsigned mask = active ? rec->mask : 0u;
   const int k = __popc(mask);
-  if (active && lt == 0) {
-    int s = 0;
-    for (unsigned m = mask; m; m &= m - 1u) {
-      const int i = __ffs(m) - 1;
-      sh.sdot[team][s] = i;
-      sh.sh[team][s] = rec->h[i];
-      ++s;
-    }
-  }
+  // slot table of the pixel: slot s = the s-th ambiguous dot (lanes in parallel)
+  if (active)
+    for (int i = lt; i < n; i += T)
+      if ((mask >> i) & 1u) {
+        const int s = __popc(mask & ((1u << i) - 1u));
+        sh.sdot[team][s] = i;
+        sh.sh[team][s] = rec->h[i];
+      }
   __syncwarp();
   float m1 = kInf, m2 = kInf;
   unsigned b1 = 0u;
   unsigned long long ev = 0;
-  if (active) {
-    SlotView sv{sh.sdot[team], sh.sh[team], k, (int)rec->w};
-    search_lane<L1, L2, CLOSED, false>(sM, sv, lt, T, 0.f, nullptr, nullptr, 0u,
-                                       m1, b1, m2, ev);
-  }
+  const SlotView sv{sh.sdot[team], sh.sh[team], active ? k : 0, active ? (int)rec->w : -1};
+  // TF (teams of 8 or more lanes): search at block level and finish the
+  // winning block together; smaller teams finish each lane's best block in
+  // the lane.
+  if (active)
+    search_lane<L1, L2, CLOSED, false, TF>(sM, sv, lt, T, 0.f, nullptr, nullptr, 0u, m1, b1,
+                                           m2, ev);
+  // best (block or candidate) with its id, and the second-best minimum
   for (int off = 1; off < T; off <<= 1) {
     const float om1 = __shfl_xor_sync(kFull, m1, off);
     const unsigned ob1 = __shfl_xor_sync(kFull, b1, off);
     const float om2 = __shfl_xor_sync(kFull, m2, off);
     top2_merge(m1, b1, m2, om1, ob1, om2);
+  }
+  // candidate level inside the winning block, by the whole team; every lane
+  // of the warp takes part (the finish shuffles over the full warp), teams
+  // without a pixel or without a block keep their result
+  if (TF) {
+    float e1, e2;
+    unsigned bits;
+    team_finish<L1, L2, CLOSED>(sM, sv, lt, T, kFull, m1 < kInf ? b1 : 0u, e1, bits, e2);
+    if (m1 < kInf) {
+      m1 = e1;
+      b1 = bits;
+      m2 = fminf(m2, e2);
+    }
   }
 
   // epilogue: n* = base + bits, U(n*) = 1/2 r^T M r in double-float (team
@@ -359,9 +375,13 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
   df u = {0.f, 0.f};
   unsigned flags = 0u;
   if (active) {
-    for (int i = lt; i < n; i += T) {
+    // rows i split over nc column chunks so that every lane of the team works
+    const int nc = T >= 2 * n ? T / n : 1;
+    const int cw = (n + nc - 1) / nc;
+    for (int task = lt; task < n * nc; task += T) {
+      const int i = task / nc, j0 = (task % nc) * cw, j1 = min(n, j0 + cw);
       df acc = {0.f, 0.f};
-      for (int j = 0; j < n; ++j) {
+      for (int j = j0; j < j1; ++j) {
         int nj = rec->base[j];
         if ((mask >> j) & 1u) nj += (int)((b1 >> __popc(mask & ((1u << j) - 1u))) & 1u);
         const df rj = df_sub({(float)nj, 0.f}, {rec->chi[j], rec->clo[j]});
@@ -371,8 +391,10 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
       if ((mask >> i) & 1u) ni += (int)((b1 >> __popc(mask & ((1u << i) - 1u))) & 1u);
       const df ri = df_sub({(float)ni, 0.f}, {rec->chi[i], rec->clo[i]});
       u = df_add(u, df_mul(acc, ri));
-      if (ni > 127) { ni = 127; flags |= kFlagOverflow; }
-      a.out_n[p * n + i] = (int8_t)ni;
+      if (j0 == 0) {
+        if (ni > 127) { ni = 127; flags |= kFlagOverflow; }
+        a.out_n[p * n + i] = (int8_t)ni;
+      }
     }
   }
   for (int off = 1; off < T; off <<= 1) {

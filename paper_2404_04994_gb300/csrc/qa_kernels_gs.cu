@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch L) {
   }
 }
 
-template <int L1, int L2, bool CLOSED>
+template <int L1, int L2, bool CLOSED, bool TF>
 __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch L) {
   __shared__ SearchShared sh;
   const ArrayDesc& a = L.one;
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch L) {
   __syncthreads();
   SearchAcc acc;
   const long long team_base = (long long)blockIdx.x * (kSearchThreads / a.cfg.T);
-  search_tile<L1, L2, CLOSED>(L, a, sh, 0, team_base, a.sc.P, acc);
+  search_tile<L1, L2, CLOSED, TF>(L, a, sh, 0, team_base, a.sc.P, acc);
   if (threadIdx.x == 0) {
     BlockCounts& o = L.bc_search[blockIdx.x];
     o.evaluated = acc.evaluated;
@@ -110,7 +110,10 @@ static cudaError_t run(const GsLaunch& L, cudaStream_t st) {
   cudaMemsetAsync(L.cnt, 0, sizeof(Counters), st);
   k_prep<CLOSED><<<prep_blocks(L), kPrepThreads, 0, st>>>(L);
   if (L.ev) cudaEventRecord(L.ev[1], st);
-  k_search<L1, L2, CLOSED><<<search_blocks(L), kSearchThreads, 0, st>>>(L);
+  if (L.one.cfg.T >= kTeamFinishMin)
+    k_search<L1, L2, CLOSED, true><<<search_blocks(L), kSearchThreads, 0, st>>>(L);
+  else
+    k_search<L1, L2, CLOSED, false><<<search_blocks(L), kSearchThreads, 0, st>>>(L);
   if (L.ev) cudaEventRecord(L.ev[2], st);
   launch_lists(L, st);
   if (L.ev) cudaEventRecord(L.ev[3], st);

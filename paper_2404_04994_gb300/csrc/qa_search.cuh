@@ -168,7 +168,9 @@ __device__ __forceinline__ void state_add(const float* sM, const SlotView& sv,
 // pattern b1, and the second-best energy m2 over the lane's candidates.
 // COLLECT: instead, append every (outer, middle) block whose minimum is
 // <= thr to blist (used by the FP64 recheck to shortlist candidates).
-template <int L1, int L2, bool CLOSED, bool COLLECT>
+// BLOCKS: return the lane's best block minimum with its block id and the
+// second-best block minimum, for a team-level finish (team_finish).
+template <int L1, int L2, bool CLOSED, bool COLLECT, bool BLOCKS = false>
 __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
                                             const SlotView sv, int t, int T,
                                             float thr, unsigned* blist,
@@ -308,6 +310,12 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
   }
   evaluated += (unsigned long long)niter * (unsigned)nsteps * (unsigned)NI;
   if (COLLECT) return;
+  if (BLOCKS) {  // block level only: the team finishes the winning block
+    m1 = g1;
+    b1 = blk;
+    m2 = g2;
+    return;
+  }
 
   m1 = kInf;
   b1 = 0u;
@@ -335,6 +343,93 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
   m1 = best;
   b1 = Sbits | bb;
   m2 = fminf(g2, second);
+}
+
+// Team-level finish of a block-level search: every lane of the team (lane lt
+// of T, T a power of two, all in one warp segment `tmask`) holds the winning
+// block id blk (after the team's top-two merge).  Every lane named by tmask
+// must call (the team reductions are shuffles); a lane whose team has no
+// pixel passes an empty slot view (k = 0) and any blk.  The block's rest state
+// (A, q) is summed over the team -- lane s adds slot s's terms -- and the
+// lanes then evaluate the block's 2^L1 inner patterns (lane lt takes
+// b = lt, lt + T, ...).  Returns the best energy e1, its full slot pattern and
+// the in-block runner-up e2; ties go to the lexicographically smaller charge
+// vector (bit-reversed pattern order).
+template <int L1, int L2, bool CLOSED>
+__device__ __forceinline__ void team_finish(const float* __restrict__ sM, const SlotView sv,
+                                            int lt, int T, unsigned tmask, unsigned blk,
+                                            float& e1, unsigned& bits1, float& e2) {
+  constexpr int NI = 1 << L1;
+  constexpr int NM = 1 << L2;
+  const int k = sv.k;
+  const unsigned o = blk >> L2, mp = blk & (unsigned)(NM - 1);
+  const unsigned Sbits = (o << (L1 + L2)) | (mp << L1);
+  float A = 0.f, q[L1 > 0 ? L1 : 1];
+#pragma unroll
+  for (int j = 0; j < L1; ++j) q[j] = 0.f;
+  for (int s = lt; s < kMaxDot; s += T) {
+    if (!((Sbits >> s) & 1u)) continue;
+    const int d = sv.dot[s];
+    const float* Mrow = sM + d * kLdM;
+    float add = sv.h[s] + 0.5f * Mrow[d];
+    for (unsigned prev = Sbits & ((1u << s) - 1u); prev; prev &= prev - 1u)
+      add += Mrow[sv.dot[__ffs(prev) - 1]];
+    A += add;
+#pragma unroll
+    for (int j = 0; j < L1; ++j)
+      if (j < k) q[j] += Mrow[sv.dot[j]];
+  }
+  for (int off = 1; off < T; off <<= 1) {
+    A += __shfl_xor_sync(tmask, A, off, T);
+#pragma unroll
+    for (int j = 0; j < L1; ++j) q[j] += __shfl_xor_sync(tmask, q[j], off, T);
+  }
+#pragma unroll
+  for (int j = 0; j < L1; ++j) {
+    if (j < k) {
+      const int d = sv.dot[j];
+      q[j] += sv.h[j] + 0.5f * sM[d * kLdM + d];
+    } else {
+      q[j] = kBig;  // dummy slot: never wins
+    }
+  }
+  const int r = CLOSED ? sv.w - __popc(Sbits) : 0;
+  e1 = kInf;
+  e2 = kInf;
+  unsigned bb = 0xffffffffu;
+  for (int b = lt; b < NI; b += T) {
+    if (CLOSED && __popc((unsigned)b) != r) continue;
+    float e = A;
+    float pb = 0.f;
+#pragma unroll
+    for (int j = 0; j < L1; ++j) {
+      if (!((b >> j) & 1)) continue;
+      e += q[j];
+      if (j < k) {
+        const float* Mrow = sM + sv.dot[j] * kLdM;
+        for (int l = 0; l < j; ++l)
+          if ((b >> l) & 1) pb += Mrow[sv.dot[l]];
+      }
+    }
+    e += pb;
+    if (e < e1 || (e == e1 && __brev((unsigned)b) < __brev(bb))) {
+      e2 = e1;
+      e1 = e;
+      bb = (unsigned)b;
+    } else if (e < e2) {
+      e2 = e;
+    }
+  }
+  for (int off = 1; off < T; off <<= 1) {
+    const float o1 = __shfl_xor_sync(tmask, e1, off, T);
+    const float o2 = __shfl_xor_sync(tmask, e2, off, T);
+    const unsigned ob = __shfl_xor_sync(tmask, bb, off, T);
+    const bool take = o1 < e1 || (o1 == e1 && __brev(ob) < __brev(bb));
+    const float lose = take ? e1 : o1;
+    e2 = fminf(fminf(e2, o2), lose);
+    if (take) { e1 = o1; bb = ob; }
+  }
+  bits1 = Sbits | (bb == 0xffffffffu ? 0u : bb);
 }
 
 // Top-two merge of (m1, b1, m2) triples; FP32 ties go to the pattern whose
