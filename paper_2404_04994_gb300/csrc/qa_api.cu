@@ -127,10 +127,13 @@ void fill_consts(int n, qa::ModelData* md) {
       const qa::df m = split(md->M[i * n + j]);
       k.Mhi[i * qa::kLdM + j] = m.hi;
       k.Mlo[i * qa::kLdM + j] = m.lo;
-      k.Cdd[i * qa::kLdM + j] = (float)md->Cdd[i * n + j];
+      const qa::df cd = split(md->Cdd[i * n + j]);
+      k.Cdd[i * qa::kLdM + j] = cd.hi;
+      k.CddLo[i * qa::kLdM + j] = cd.lo;
       r += md->Cdd[i * n + j];
     }
     k.sv[i] = (float)r;
+    k.sv2[i] = split(r);
     k.vs[i] = split(md->vs[i]);
     tot += r;
   }
@@ -138,6 +141,10 @@ void fill_consts(int n, qa::ModelData* md) {
   // decision margin of an FP32 QP minimum: 8 cond(Cdd) (n + 1) u32 per unit
   // of (1 + max|c| + N_hat)
   k.bx_qp_scale = (float)(8.0 * md->cond * (n + 1) * 5.9604644775390625e-8);
+  // after one refinement step with double-float residuals the error is the
+  // square of the FP32 one (per unit of the same scale)
+  const double e1 = md->cond * (n + 1) * 5.9604644775390625e-8;
+  k.bx_qp_scale2 = (float)(8.0 * e1 * e1);
   k.model_bad = md->status != 0;
 }
 

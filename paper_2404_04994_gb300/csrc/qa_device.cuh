@@ -103,6 +103,10 @@ struct __align__(16) ModelConsts {
   float bx_qp_scale;           // QP decision margin per unit of (1+|c|+N_hat)
   int model_bad;               // device Cholesky of an updated Cdd failed
   int pad;
+  float CddLo[kMaxDot * kLdM]; // Cdd - hi part (Cdd as double-float with Cdd above)
+  df sv2[kMaxDot];             // Cdd 1 as double-float
+  float bx_qp_scale2;          // ... after one double-float refinement of the QP
+  int pad2[3];
 };
 
 // Device copy of a model (written by the host or by the Cholesky kernel).

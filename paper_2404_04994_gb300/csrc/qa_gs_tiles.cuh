@@ -79,8 +79,12 @@ struct PrepShared {
   ModelConsts cs;
   df sV[kMaxGate], sU[kMaxGate], sW[kMaxGate];
   df sc0[kMaxDot], sdu[kMaxDot], sdw[kMaxDot];
-  float sx[kPrepThreads];
-  int sst[kPrepThreads];
+  float qK[kPrepThreads][kQPRow];  // team QP: KKT rows, active lists, unknowns, c
+  int qa[kPrepThreads];
+  float qz[kPrepThreads];
+  float qzl[kPrepThreads];
+  float qx[kPrepThreads];
+  float qc[kPrepThreads];
   unsigned long long red64[kPrepThreads / 32];
   unsigned red32[kPrepThreads / 32];
 };
@@ -189,20 +193,30 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
     } else {
       const float scale = 1.f + cmax + (float)nhat;
       bx = fmaxf(bx, bx_qp_scale * scale);
-      sh.sx[threadIdx.x] = c.hi + c.lo;
-      __syncwarp(tmask);
-      if (lt == 0) {
-        float cf[kMaxDot], xf[kMaxDot];
-        for (int j = 0; j < n; ++j) cf[j] = sh.sx[threadIdx.x + j];
-        const int st = qp_active_set<float>(n, sh.cs.Cdd, kLdM, cf, CLOSED, (float)nhat,
-                                            sh.cs.sv, sh.cs.s_s, A, 0.25f * bx_qp_scale * scale,
-                                            4 * n + 4, xf);
-        for (int j = 0; j < n; ++j) sh.sx[threadIdx.x + j] = xf[j];
-        sh.sst[threadIdx.x] = st;
+      float xf = 0.f;
+      unsigned Af = 0u;
+      const int tb = threadIdx.x - lt;
+      const int st = qp_team<CLOSED>(n, lt, TP, tmask, tb, sh.cs.Cdd, sh.cs.sv, sh.cs.s_s,
+                                     live ? c.hi + c.lo : 0.f, (float)nhat, A,
+                                     0.25f * bx_qp_scale * scale, 4 * n + 4, sh.qK, sh.qa,
+                                     sh.qz, sh.qc, xf, Af);
+      if (st != 0) {
+        flags |= kFlagQPCap;
+        if (live) x = {xf, 0.f};
+      } else {
+        // one double-float refinement: the margin shrinks to the square of
+        // the FP32 one; a multiplier or free x_i below -margin at that
+        // precision leaves the active set (and x) to the FP64 recheck
+        const float bx2 = fmaxf(a.bx_analytic, sh.cs.bx_qp_scale2 * scale);
+        df xr;
+        const int bad = qp_team_refine<CLOSED>(n, lt, TP, tmask, tb, sh.cs.Cdd, sh.cs.CddLo,
+                                               sh.cs.sv2, live ? c : df{0.f, 0.f}, (float)nhat,
+                                               Af, 0.25f * bx2, sh.qK, sh.qa, sh.qz, sh.qzl,
+                                               sh.qx, xr);
+        if (live) x = xr;
+        if (bad) flags |= kFlagBoundary;
+        else bx = bx2;
       }
-      __syncwarp(tmask);
-      if (live) x = {sh.sx[threadIdx.x], 0.f};
-      if (sh.sst[threadIdx.x - lt] != 0) flags |= kFlagQPCap;
       __syncwarp(tmask);
     }
   }

@@ -6,6 +6,8 @@
 
 namespace qa {
 
+constexpr int kQPRow = kMaxDot + 1;  // row length of the team QP's shared KKT rows
+
 // ---------------------------------------------------------------------------
 // Continuous minimum when the analytic one is infeasible (Sec. III.A.2).
 //
@@ -92,6 +94,184 @@ __device__ __noinline__ int qp_active_set(int n, const T* Cdd, int ldc,
     return 0;
   }
   return -1;
+}
+
+// ---------------------------------------------------------------------------
+// The same active-set method, run by a team of TP lanes (TP a power of two,
+// TP >= n; lane i owns dot i; `tmask` the team's lanes of the warp, `tbase`
+// the index of the team's first thread in the block).  Row p of the bordered
+// KKT matrix lives in the shared row Ks[tbase + p][.] and is owned by lane p:
+// the Cholesky factor is built column by column (lane j the pivot, lanes
+// below it their entries, a dot product each), and both triangular solves
+// proceed one unknown at a time with a shuffle broadcast, so the serial chain
+// is O(m^2) instead of O(m^3).  Active-set decisions are team ballots.
+// Returns 0 with x_i in lane i, or -1 (no PD system, or no settling within
+// cap iterations).  Every lane of tmask must call.
+// ---------------------------------------------------------------------------
+template <bool CLOSED>
+__device__ __forceinline__ int qp_team(int n, int lt, int TP, unsigned tmask, int tbase,
+                                       const float* Cdd, const float* v, float s, float ci,
+                                       float nhat, unsigned A, float tol, int cap,
+                                       float (*Ks)[kQPRow], int* alist, float* zs, float* cs,
+                                       float& x, unsigned& Afinal) {
+  const bool live = lt < n;
+  cs[tbase + lt] = live ? ci : 0.f;
+  float csum = live ? ci : 0.f;
+  for (int off = 1; off < TP; off <<= 1) csum += __shfl_xor_sync(tmask, csum, off, TP);
+  for (int it = 0; it < cap; ++it) {
+    const int m = __popc(A);
+    if (CLOSED && m == n) return -1;
+    const int ms = m + (CLOSED ? 1 : 0);
+    const bool act = live && ((A >> lt) & 1u);
+    if (act) alist[tbase + __popc(A & ((1u << lt) - 1u))] = lt;
+    __syncwarp(tmask);
+    // row lt of K and its right-hand side
+    float y = 0.f;
+    if (lt < m) {
+      const int ap = alist[tbase + lt];
+      for (int q = 0; q <= lt; ++q) Ks[tbase + lt][q] = Cdd[ap * kLdM + alist[tbase + q]];
+      y = -cs[tbase + ap];
+    } else if (CLOSED && lt == m) {
+      for (int q = 0; q < m; ++q) Ks[tbase + lt][q] = v[alist[tbase + q]];
+      Ks[tbase + lt][m] = s;
+      y = nhat - csum;
+    }
+    __syncwarp(tmask);
+    // Cholesky, column by column
+    bool ok = true;
+    for (int j = 0; j < ms; ++j) {
+      if (lt == j) {
+        float d = Ks[tbase + j][j];
+        for (int q = 0; q < j; ++q) d -= Ks[tbase + j][q] * Ks[tbase + j][q];
+        Ks[tbase + j][j] = d > 0.f ? sqrtf(d) : 0.f;
+      }
+      __syncwarp(tmask);
+      const float ljj = Ks[tbase + j][j];
+      if (!(ljj > 0.f)) { ok = false; break; }
+      if (lt > j && lt < ms) {
+        float e = Ks[tbase + lt][j];
+        for (int q = 0; q < j; ++q) e -= Ks[tbase + lt][q] * Ks[tbase + j][q];
+        Ks[tbase + lt][j] = e / ljj;
+      }
+      __syncwarp(tmask);
+    }
+    if (!ok) return -1;
+    // L y = rhs, then L^T z = y (lane p holds unknown p)
+    for (int q = 0; q < ms; ++q) {
+      if (lt == q) y /= Ks[tbase + q][q];
+      const float yq = __shfl_sync(tmask, y, tbase % 32 + q);
+      if (lt > q && lt < ms) y -= Ks[tbase + lt][q] * yq;
+    }
+    for (int q = ms - 1; q >= 0; --q) {
+      if (lt == q) y /= Ks[tbase + q][q];
+      const float zq = __shfl_sync(tmask, y, tbase % 32 + q);
+      if (lt < q) y -= Ks[tbase + q][lt] * zq;
+    }
+    if (lt < ms) zs[tbase + lt] = y;
+    __syncwarp(tmask);
+    const float lam = CLOSED ? zs[tbase + m] : 0.f;
+    float xi = 0.f;
+    if (live && !act) {
+      xi = ci + (CLOSED ? lam * v[lt] : 0.f);
+      for (int p = 0; p < m; ++p) xi += Cdd[lt * kLdM + alist[tbase + p]] * zs[tbase + p];
+    }
+    const unsigned neg =
+        (__ballot_sync(tmask, live && !act && xi < -tol) & tmask) >> (tbase % 32);
+    __syncwarp(tmask);
+    if (neg) { A |= neg; continue; }
+    // most negative multiplier leaves the active set
+    float zw = (lt < m) ? zs[tbase + lt] : 0.f;
+    int wdot = (lt < m && zw < -tol) ? alist[tbase + lt] : -1;
+    if (wdot < 0) zw = 0.f;
+    for (int off = 1; off < TP; off <<= 1) {
+      const float oz = __shfl_xor_sync(tmask, zw, off, TP);
+      const int od = __shfl_xor_sync(tmask, wdot, off, TP);
+      if (od >= 0 && (wdot < 0 || oz < zw || (oz == zw && od < wdot))) { zw = oz; wdot = od; }
+    }
+    __syncwarp(tmask);
+    if (wdot >= 0) { A &= ~(1u << wdot); continue; }
+    x = (live && !act) ? fmaxf(xi, 0.f) : 0.f;
+    Afinal = A;
+    return 0;
+  }
+  return -1;
+}
+
+// One step of iterative refinement of a settled team QP (active set A, FP32
+// multipliers in zs, the FP32 Cholesky factor of the bordered KKT matrix
+// still in Ks): x is formed in double-float from c, Cdd (hi + lo) and the
+// multipliers; the KKT residual (x_a for active a, N_hat - 1^T x closed) is
+// solved for a correction with the same factor; x is formed again from the
+// corrected multipliers (double-float).  The error of x drops from about
+// cond(Cdd) u to (cond(Cdd) u)^2.  Returns nonzero when, at this precision,
+// a free x_i or a multiplier is below -tol (the active set is then in doubt).
+// Every lane of tmask must call; lane i returns x_i (0 for active dots).
+template <bool CLOSED>
+__device__ __forceinline__ int qp_team_refine(int n, int lt, int TP, unsigned tmask, int tbase,
+                                              const float* CddHi, const float* CddLo,
+                                              const df* v2, df ci, float nhat, unsigned A,
+                                              float tol, float (*Ks)[kQPRow], const int* alist,
+                                              float* zs, float* zl, float* xr, df& x) {
+  const bool live = lt < n;
+  const int m = __popc(A);
+  const int ms = m + (CLOSED ? 1 : 0);
+  const bool act = live && ((A >> lt) & 1u);
+  auto form_x = [&](bool with_lo) {
+    df xi = live ? ci : df{0.f, 0.f};
+    if (live) {
+      if (CLOSED) {
+        const df lam = {zs[tbase + m], with_lo ? zl[tbase + m] : 0.f};
+        xi = df_add(xi, df_mul(v2[lt], lam));
+      }
+      for (int p = 0; p < m; ++p) {
+        const int ap = alist[tbase + p];
+        const df cd = {CddHi[lt * kLdM + ap], CddLo[lt * kLdM + ap]};
+        const df zp = {zs[tbase + p], with_lo ? zl[tbase + p] : 0.f};
+        xi = df_add(xi, df_mul(cd, zp));
+      }
+    }
+    return xi;
+  };
+  df xi = form_x(false);
+  xr[tbase + lt] = xi.hi + xi.lo;
+  df xsum = xi;
+  for (int off = 1; off < TP; off <<= 1) {
+    df o;
+    o.hi = __shfl_xor_sync(tmask, xsum.hi, off, TP);
+    o.lo = __shfl_xor_sync(tmask, xsum.lo, off, TP);
+    xsum = df_add(xsum, o);
+  }
+  __syncwarp(tmask);
+  float y = 0.f;
+  if (lt < m) y = -xr[tbase + alist[tbase + lt]];
+  else if (CLOSED && lt == m) {
+    const df r = df_sub({nhat, 0.f}, xsum);
+    y = r.hi + r.lo;
+  }
+  for (int q = 0; q < ms; ++q) {
+    if (lt == q) y /= Ks[tbase + q][q];
+    const float yq = __shfl_sync(tmask, y, tbase % 32 + q);
+    if (lt > q && lt < ms) y -= Ks[tbase + lt][q] * yq;
+  }
+  for (int q = ms - 1; q >= 0; --q) {
+    if (lt == q) y /= Ks[tbase + q][q];
+    const float zq = __shfl_sync(tmask, y, tbase % 32 + q);
+    if (lt < q) y -= Ks[tbase + q][lt] * zq;
+  }
+  if (lt < ms) {
+    const df zc = two_sum(zs[tbase + lt], y);
+    zs[tbase + lt] = zc.hi;
+    zl[tbase + lt] = zc.lo;
+  }
+  __syncwarp(tmask);
+  xi = act ? df{0.f, 0.f} : form_x(true);
+  const bool bad = (live && !act && xi.hi + xi.lo < -tol) ||
+                   (lt < m && zs[tbase + lt] + zl[tbase + lt] < -tol);
+  const unsigned anybad = __ballot_sync(tmask, bad) & tmask;
+  __syncwarp(tmask);
+  if (xi.hi < 0.f || (xi.hi == 0.f && xi.lo < 0.f)) xi = {0.f, 0.f};
+  x = xi;
+  return anybad != 0u;
 }
 
 // ---------------------------------------------------------------------------

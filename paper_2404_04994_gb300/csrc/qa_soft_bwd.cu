@@ -94,12 +94,15 @@ __global__ void k_model_update(ModelData* md, int n, int ng, const double* Cdd,
     const df m = live ? df_from_double(md->M[i * n + j]) : df{0.f, 0.f};
     k.Mhi[e] = m.hi;
     k.Mlo[e] = m.lo;
-    k.Cdd[e] = live ? __double2float_rn(md->Cdd[i * n + j]) : 0.f;
+    const df cd = live ? df_from_double(md->Cdd[i * n + j]) : df{0.f, 0.f};
+    k.Cdd[e] = cd.hi;
+    k.CddLo[e] = cd.lo;
   }
   if (tid < kMaxDot) {
     double r = 0.0;
     for (int j = 0; j < n && tid < n; ++j) r += md->Cdd[tid * n + j];
     k.sv[tid] = __double2float_rn(r);
+    k.sv2[tid] = tid < n ? df_from_double(r) : df{0.f, 0.f};
     k.vs[tid] = tid < n ? df_from_double(md->vs[tid]) : df{0.f, 0.f};
   }
   if (tid == 0) {
@@ -107,6 +110,9 @@ __global__ void k_model_update(ModelData* md, int n, int ng, const double* Cdd,
     for (int e = 0; e < n * n; ++e) tot += md->Cdd[e];
     k.s_s = __double2float_rn(tot);
     k.bx_qp_scale = __double2float_rn(8.0 * md->cond * (n + 1) * 5.9604644775390625e-8);
+    const double e1 = md->cond * (n + 1) * 5.9604644775390625e-8;
+    k.bx_qp_scale2 = __double2float_rn(8.0 * e1 * e1);
+    k.pad2[0] = k.pad2[1] = k.pad2[2] = 0;
     k.model_bad = md->status != 0;
     k.pad = 0;
   }
