@@ -86,7 +86,8 @@ struct __align__(16) PixRec {
   unsigned char k;      // popcount(mask)
   signed char w;        // closed: number of ambiguous dots taking +1; open: -1
   unsigned char flags;  // QA flag bits from the prep stage
-  unsigned char pad0[3];
+  unsigned char pad0;
+  unsigned short qpA;   // QP pixels: the active set the FP32 QP settled on
   float bound;          // FP32 gap below which the pixel is a near-tie
 };
 

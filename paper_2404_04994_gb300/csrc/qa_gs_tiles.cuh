@@ -184,6 +184,7 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
   const unsigned A =
       tballot(live && (x.hi < 0.f || (x.hi == 0.f && x.lo < 0.f)));
   unsigned flags = 0u;
+  unsigned qp_set = 0u;
   float bx = a.bx_analytic;
   const float cmax = tmax_f(live ? fabsf(c.hi + c.lo) : 0.f);
   if (A) {  // (a3) QP, solved by the team's first lane
@@ -196,8 +197,8 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
       float xf = 0.f;
       unsigned Af = 0u;
       const int tb = threadIdx.x - lt;
-      const int st = qp_team<CLOSED>(n, lt, TP, tmask, tb, sh.cs.Cdd, sh.cs.sv, sh.cs.s_s,
-                                     live ? c.hi + c.lo : 0.f, (float)nhat, A,
+      const int st = qp_team<float, CLOSED>(n, lt, TP, tmask, tb, sh.cs.Cdd, kLdM, sh.cs.sv,
+                                            sh.cs.s_s, live ? c.hi + c.lo : 0.f, (float)nhat, A,
                                      0.25f * bx_qp_scale * scale, 4 * n + 4, sh.qK, sh.qa,
                                      sh.qz, sh.qc, xf, Af);
       if (st != 0) {
@@ -216,6 +217,7 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
         if (live) x = xr;
         if (bad) flags |= kFlagBoundary;
         else bx = bx2;
+        qp_set = Af;
       }
       __syncwarp(tmask);
     }
@@ -289,6 +291,7 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
     rec->k = (unsigned char)k;
     rec->w = (signed char)(CLOSED ? w : -1);
     rec->flags = (unsigned char)flags;
+    rec->qpA = (unsigned short)qp_set;
     rec->bound = near_tie_bound(S, k, a.cfg.L2);
     my_cand = CLOSED ? binom(k, w) : (1ull << k);
     my_qp = (flags & kFlagQP) ? 1u : 0u;
@@ -618,6 +621,10 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
 //      lexicographically smallest charge vector.
 // ---------------------------------------------------------------------------
 struct RecheckShared {
+  double qK[32][kQPRow];  // FP64 team QP of warp 0
+  int qa[32];
+  double qz[32], qc[32], v64[kMaxDot], sx64[kMaxDot];
+  int sqp;
   float sM[kMaxDot * kLdM];
   int sdot[kMaxDot];
   float sh[kMaxDot];
@@ -662,13 +669,52 @@ __device__ inline void recheck_entry(const GsLaunch& L, const ArrayDesc& a, Rech
   const long long p = fe.p;
   if (tid < n) sc64[tid] = pixel_c_f64(a.md, a.ng, a.sc, a.mt.carrier, p, tid);
   __syncthreads();
+  if (tid < 32) {
+    // continuous minimum in FP64 by warp 0, lane i owning dot i: analytic
+    // (Appendix C / D), else the team active-set QP
+    const int lt = tid;
+    const bool live = lt < n;
+    const double ci = live ? sc64[lt] : 0.0;
+    double csum = ci, cmax = live ? fabs(ci) : 0.0;
+    for (int off = 1; off < 32; off <<= 1) {
+      csum += __shfl_xor_sync(kFull, csum, off);
+      cmax = fmax(cmax, __shfl_xor_sync(kFull, cmax, off));
+    }
+    const double nh = (double)a.mt.n_charges;
+    double x = CLOSED ? ci + (nh - csum) * (live ? a.md->vs[lt] : 0.0) : ci;
+    const unsigned A = __ballot_sync(kFull, live && x < 0.0);
+    int st = 0;
+    if (A) {
+      if (CLOSED && a.mt.n_charges == 0) {
+        x = 0.0;
+      } else {
+        double vi = 0.0;
+        if (live)
+          for (int j = 0; j < n; ++j) vi += a.md->Cdd[lt * n + j];
+        if (lt < kMaxDot) S.v64[lt] = vi;
+        double s = vi;
+        for (int off = 1; off < 32; off <<= 1) s += __shfl_xor_sync(kFull, s, off);
+        __syncwarp();
+        unsigned Af = 0u;
+        const double tol = 1e-12 * (fmax(cmax, 1.0) + nh);
+        // warm start from the active set the FP32 QP settled on, if any
+        const unsigned A0 = a.recs[p].qpA ? (unsigned)a.recs[p].qpA : A;
+        st = qp_team<double, CLOSED>(n, lt, 32, kFull, 0, a.md->Cdd, n, S.v64, s, ci, nh, A0,
+                                     tol, 8 * n + 8, S.qK, S.qa, S.qz, S.qc, x, Af);
+      }
+    }
+    if (live) S.sx64[lt] = x;
+    if (lt == 0) S.sqp = (A ? 1 : 0) | (st != 0 ? 2 : 0);
+  }
+  __syncthreads();
   if (tid == 0) {
-    double c[kMaxDot];
     int base[kMaxDot];
-    unsigned mask = 0u, fl = 0u;
+    unsigned mask = 0u, fl = (S.sqp & 1) ? kFlagQP : 0u;
     int w = -1;
-    for (int i = 0; i < n; ++i) c[i] = sc64[i];
-    sstatus = (a.md->status != 0) ? -1 : settle_pixel_f64(a.md, n, a.mt, c, base, mask, w, fl);
+    if (a.md->status != 0 || (S.sqp & 2))
+      sstatus = -1;
+    else
+      sstatus = candidate_set_f64(n, S.sx64, a.mt.t, CLOSED, a.mt.n_charges, base, mask, w, fl);
     sflags = fl;
     smask = mask;
     sw = CLOSED ? w : -1;

@@ -106,17 +106,20 @@ __device__ __noinline__ int qp_active_set(int n, const T* Cdd, int ldc,
 // proceed one unknown at a time with a shuffle broadcast, so the serial chain
 // is O(m^2) instead of O(m^3).  Active-set decisions are team ballots.
 // Returns 0 with x_i in lane i, or -1 (no PD system, or no settling within
-// cap iterations).  Every lane of tmask must call.
+// cap iterations).  T = float (prep) or double (FP64 recheck); Cdd has row
+// stride ldc.  Every lane of tmask must call.
 // ---------------------------------------------------------------------------
-template <bool CLOSED>
+__device__ __forceinline__ float qsqrt(float v) { return sqrtf(v); }
+__device__ __forceinline__ double qsqrt(double v) { return sqrt(v); }
+
+template <typename T, bool CLOSED>
 __device__ __forceinline__ int qp_team(int n, int lt, int TP, unsigned tmask, int tbase,
-                                       const float* Cdd, const float* v, float s, float ci,
-                                       float nhat, unsigned A, float tol, int cap,
-                                       float (*Ks)[kQPRow], int* alist, float* zs, float* cs,
-                                       float& x, unsigned& Afinal) {
+                                       const T* Cdd, int ldc, const T* v, T s, T ci, T nhat,
+                                       unsigned A, T tol, int cap, T (*Ks)[kQPRow], int* alist,
+                                       T* zs, T* cs, T& x, unsigned& Afinal) {
   const bool live = lt < n;
-  cs[tbase + lt] = live ? ci : 0.f;
-  float csum = live ? ci : 0.f;
+  cs[tbase + lt] = live ? ci : (T)0;
+  T csum = live ? ci : (T)0;
   for (int off = 1; off < TP; off <<= 1) csum += __shfl_xor_sync(tmask, csum, off, TP);
   for (int it = 0; it < cap; ++it) {
     const int m = __popc(A);
@@ -126,10 +129,10 @@ __device__ __forceinline__ int qp_team(int n, int lt, int TP, unsigned tmask, in
     if (act) alist[tbase + __popc(A & ((1u << lt) - 1u))] = lt;
     __syncwarp(tmask);
     // row lt of K and its right-hand side
-    float y = 0.f;
+    T y = 0;
     if (lt < m) {
       const int ap = alist[tbase + lt];
-      for (int q = 0; q <= lt; ++q) Ks[tbase + lt][q] = Cdd[ap * kLdM + alist[tbase + q]];
+      for (int q = 0; q <= lt; ++q) Ks[tbase + lt][q] = Cdd[ap * ldc + alist[tbase + q]];
       y = -cs[tbase + ap];
     } else if (CLOSED && lt == m) {
       for (int q = 0; q < m; ++q) Ks[tbase + lt][q] = v[alist[tbase + q]];
@@ -141,15 +144,15 @@ __device__ __forceinline__ int qp_team(int n, int lt, int TP, unsigned tmask, in
     bool ok = true;
     for (int j = 0; j < ms; ++j) {
       if (lt == j) {
-        float d = Ks[tbase + j][j];
+        T d = Ks[tbase + j][j];
         for (int q = 0; q < j; ++q) d -= Ks[tbase + j][q] * Ks[tbase + j][q];
-        Ks[tbase + j][j] = d > 0.f ? sqrtf(d) : 0.f;
+        Ks[tbase + j][j] = d > (T)0 ? qsqrt(d) : (T)0;
       }
       __syncwarp(tmask);
-      const float ljj = Ks[tbase + j][j];
-      if (!(ljj > 0.f)) { ok = false; break; }
+      const T ljj = Ks[tbase + j][j];
+      if (!(ljj > (T)0)) { ok = false; break; }
       if (lt > j && lt < ms) {
-        float e = Ks[tbase + lt][j];
+        T e = Ks[tbase + lt][j];
         for (int q = 0; q < j; ++q) e -= Ks[tbase + lt][q] * Ks[tbase + j][q];
         Ks[tbase + lt][j] = e / ljj;
       }
@@ -159,38 +162,38 @@ __device__ __forceinline__ int qp_team(int n, int lt, int TP, unsigned tmask, in
     // L y = rhs, then L^T z = y (lane p holds unknown p)
     for (int q = 0; q < ms; ++q) {
       if (lt == q) y /= Ks[tbase + q][q];
-      const float yq = __shfl_sync(tmask, y, tbase % 32 + q);
+      const T yq = __shfl_sync(tmask, y, tbase % 32 + q);
       if (lt > q && lt < ms) y -= Ks[tbase + lt][q] * yq;
     }
     for (int q = ms - 1; q >= 0; --q) {
       if (lt == q) y /= Ks[tbase + q][q];
-      const float zq = __shfl_sync(tmask, y, tbase % 32 + q);
+      const T zq = __shfl_sync(tmask, y, tbase % 32 + q);
       if (lt < q) y -= Ks[tbase + q][lt] * zq;
     }
     if (lt < ms) zs[tbase + lt] = y;
     __syncwarp(tmask);
-    const float lam = CLOSED ? zs[tbase + m] : 0.f;
-    float xi = 0.f;
+    const T lam = CLOSED ? zs[tbase + m] : (T)0;
+    T xi = 0;
     if (live && !act) {
-      xi = ci + (CLOSED ? lam * v[lt] : 0.f);
-      for (int p = 0; p < m; ++p) xi += Cdd[lt * kLdM + alist[tbase + p]] * zs[tbase + p];
+      xi = ci + (CLOSED ? lam * v[lt] : (T)0);
+      for (int p = 0; p < m; ++p) xi += Cdd[lt * ldc + alist[tbase + p]] * zs[tbase + p];
     }
     const unsigned neg =
         (__ballot_sync(tmask, live && !act && xi < -tol) & tmask) >> (tbase % 32);
     __syncwarp(tmask);
     if (neg) { A |= neg; continue; }
     // most negative multiplier leaves the active set
-    float zw = (lt < m) ? zs[tbase + lt] : 0.f;
+    T zw = (lt < m) ? zs[tbase + lt] : (T)0;
     int wdot = (lt < m && zw < -tol) ? alist[tbase + lt] : -1;
-    if (wdot < 0) zw = 0.f;
+    if (wdot < 0) zw = 0;
     for (int off = 1; off < TP; off <<= 1) {
-      const float oz = __shfl_xor_sync(tmask, zw, off, TP);
+      const T oz = __shfl_xor_sync(tmask, zw, off, TP);
       const int od = __shfl_xor_sync(tmask, wdot, off, TP);
       if (od >= 0 && (wdot < 0 || oz < zw || (oz == zw && od < wdot))) { zw = oz; wdot = od; }
     }
     __syncwarp(tmask);
     if (wdot >= 0) { A &= ~(1u << wdot); continue; }
-    x = (live && !act) ? fmaxf(xi, 0.f) : 0.f;
+    x = (live && !act) ? (xi > (T)0 ? xi : (T)0) : (T)0;
     Afinal = A;
     return 0;
   }
