@@ -508,20 +508,33 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
   const unsigned mask = rec->mask;
   const int k = __popc(mask);
   const int w = rec->w;
-  // h_i = (M (base - c))_i in double-float, and U(base) = r0 . h / 2
-  if (tid < n) {
-    df hi = {0.f, 0.f};
-    for (int j = 0; j < n; ++j) {
+  // h_i = (M (base - c))_i in double-float, and U(base) = r0 . h / 2: one
+  // product M_ij r_j per thread (row i = tid / 16), summed over the row's 16
+  // threads
+  {
+    static_assert(kResolveThreads == kMaxDot * kMaxDot, "one thread per matrix entry");
+    const int i = tid >> 4, j = tid & 15;
+    df prod = {0.f, 0.f};
+    if (i < n && j < n) {
       const df rj = df_sub({(float)rec->base[j], 0.f}, {rec->chi[j], rec->clo[j]});
-      hi = df_add(hi, df_mul({sM[tid * kLdM + j], sMlo[tid * kLdM + j]}, rj));
+      prod = df_mul({sM[i * kLdM + j], sMlo[i * kLdM + j]}, rj);
     }
-    const df r0 = df_sub({(float)rec->base[tid], 0.f}, {rec->chi[tid], rec->clo[tid]});
-    sui[tid] = df_mul(hi, r0);
-    if ((mask >> tid) & 1u) {
-      const int s = __popc(mask & ((1u << tid) - 1u));
-      sdot[s] = tid;
-      sh[s] = rec->h[tid];
-      shd[s] = df_add(hi, df_mul_f({sM[tid * kLdM + tid], sMlo[tid * kLdM + tid]}, 0.5f));
+    for (int off = 1; off < 16; off <<= 1) {
+      df o;
+      o.hi = __shfl_xor_sync(kFull, prod.hi, off, 16);
+      o.lo = __shfl_xor_sync(kFull, prod.lo, off, 16);
+      prod = df_add(prod, o);
+    }
+    if (j == 0 && i < n) {
+      const df hi = prod;
+      const df r0 = df_sub({(float)rec->base[i], 0.f}, {rec->chi[i], rec->clo[i]});
+      sui[i] = df_mul(hi, r0);
+      if ((mask >> i) & 1u) {
+        const int s = __popc(mask & ((1u << i) - 1u));
+        sdot[s] = i;
+        sh[s] = rec->h[i];
+        shd[s] = df_add(hi, df_mul_f({sM[i * kLdM + i], sMlo[i * kLdM + i]}, 0.5f));
+      }
     }
   }
   if (tid == 0) bcnt = 0u;
@@ -540,22 +553,41 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
   df best = {kInf, 0.f}, second = {kInf, 0.f};
   unsigned bbits = 0xffffffffu;
   if (fits) {
-    for (unsigned idx = tid; idx < nb * NI; idx += kResolveThreads) {
-      const unsigned id = blist[idx / NI];
-      const unsigned b = idx % NI;
-      const unsigned bits = ((id >> L2) << (L1 + L2)) | ((id & (NM - 1)) << L1) | b;
-      if ((bits >> k) != 0u) continue;
-      if (CLOSED && __popc(bits) != w) continue;
-      df E = {0.f, 0.f};
-      for (unsigned m = bits; m; m &= m - 1u) {
-        const int s = __ffs(m) - 1;
-        const int d = sdot[s];
-        E = df_add(E, shd[s]);
-        for (unsigned q = bits & ((1u << s) - 1u); q; q &= q - 1u) {
-          const int d2i = sdot[__ffs(q) - 1];
-          E = df_add(E, {sM[d * kLdM + d2i], sMlo[d * kLdM + d2i]});
-        }
+    // eight threads per shortlisted candidate: thread `sub` of a group takes
+    // the set slots s with s = sub (mod 8), adding h_s + M_ss / 2 and the
+    // pair terms with the set slots below s; the group then sums its parts
+    constexpr int kSub = 8;
+    const int sub = tid & (kSub - 1), grp = tid / kSub;
+    const unsigned ncand = nb * NI;
+    for (unsigned base_idx = 0; base_idx < ncand; base_idx += kResolveThreads / kSub) {
+      const unsigned idx = base_idx + (unsigned)grp;
+      bool ok = idx < ncand;
+      unsigned bits = 0u;
+      if (ok) {
+        const unsigned id = blist[idx / NI];
+        const unsigned b = idx % NI;
+        bits = ((id >> L2) << (L1 + L2)) | ((id & (NM - 1)) << L1) | b;
+        ok = (bits >> k) == 0u && (!CLOSED || __popc(bits) == w);
       }
+      df E = {0.f, 0.f};
+      if (ok)
+        for (unsigned m = bits; m; m &= m - 1u) {
+          const int s = __ffs(m) - 1;
+          if ((s & (kSub - 1)) != sub) continue;
+          const int d = sdot[s];
+          E = df_add(E, shd[s]);
+          for (unsigned q = bits & ((1u << s) - 1u); q; q &= q - 1u) {
+            const int d2i = sdot[__ffs(q) - 1];
+            E = df_add(E, {sM[d * kLdM + d2i], sMlo[d * kLdM + d2i]});
+          }
+        }
+      for (int off = 1; off < kSub; off <<= 1) {
+        df o;
+        o.hi = __shfl_xor_sync(kFull, E.hi, off, kSub);
+        o.lo = __shfl_xor_sync(kFull, E.lo, off, kSub);
+        E = df_add(E, o);
+      }
+      if (!ok || sub != 0) continue;
       const bool better = E.hi < best.hi || (E.hi == best.hi && E.lo < best.lo) ||
                           (E.hi == best.hi && E.lo == best.lo && __brev(bits) < __brev(bbits));
       if (better) { second = best; best = E; bbits = bits; }
