@@ -315,6 +315,7 @@ struct SearchShared {
   ModelConsts cs;
   int sdot[kSearchThreads][kMaxDot];
   float sh[kSearchThreads][kMaxDot];
+  __align__(16) float colt[kSearchThreads / kTeamFinishMin][4 * kColStride];
   unsigned long long red64[kSearchThreads / 32];
   unsigned red32[kSearchThreads / 32];
 };
@@ -362,9 +363,15 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
   // TF (teams of 8 or more lanes): search at block level and finish the
   // winning block together; smaller teams finish each lane's best block in
   // the lane.
+  float* colt = TF ? sh.colt[team] : nullptr;
+  if (TF) {
+    static_assert(L2 <= 4 && L1 + L2 <= kColStride, "column table layout");
+    if (active) col_build<L1, L2>(sM, sv, lt, T, colt);
+    __syncwarp();
+  }
   if (active)
     search_lane<L1, L2, CLOSED, false, TF>(sM, sv, lt, T, 0.f, nullptr, nullptr, 0u, m1, b1,
-                                           m2, ev);
+                                           m2, ev, colt);
   // best (block or candidate) with its id, and the second-best minimum
   for (int off = 1; off < T; off <<= 1) {
     const float om1 = __shfl_xor_sync(kFull, m1, off);

@@ -104,6 +104,11 @@ __device__ __forceinline__ float inner_min_closed(float A, const float* q,
   return res;
 }
 
+// Team table of the middle-slot columns used by block-level searches: for
+// middle slot m, kColStride floats holding M(inner j, m) at j < L1 and
+// M(middle m', m) at L1 + m' (0 on the diagonal and for absent slots).
+constexpr int kColStride = 12;  // >= L1 + L2 for every split, a multiple of 4
+
 // Per-pixel slot data staged by the team: dot of each slot, h of each slot.
 struct SlotView {
   const int* dot;
@@ -176,7 +181,8 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
                                             float thr, unsigned* blist,
                                             unsigned* bcount, unsigned bcap,
                                             float& m1, unsigned& b1, float& m2,
-                                            unsigned long long& evaluated) {
+                                            unsigned long long& evaluated,
+                                            const float* __restrict__ colt = nullptr) {
   static_assert(L1 >= 2 && L1 <= 6 && L2 >= 0 && L2 <= 5, "search split");
   constexpr int NI = 1 << L1;
   constexpr int NM = 1 << L2;
@@ -225,16 +231,18 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
     dM[m] = d;
     gb[m] = live ? sv.h[L1 + m] + 0.5f * sM[d * kLdM + d] : 0.f;
   }
-#pragma unroll
-  for (int m = 0; m < L2; ++m)
-#pragma unroll
-    for (int m2 = 0; m2 < L2; ++m2)
-      Mmm[m][m2] = (m != m2 && m < nmid && m2 < nmid) ? sM[dM[m] * kLdM + dM[m2]] : 0.f;
-#pragma unroll
-  for (int j = 0; j < L1; ++j)
+  if (!BLOCKS) {  // BLOCKS: the middle columns come from the team table colt
 #pragma unroll
     for (int m = 0; m < L2; ++m)
-      Mim[j][m] = (m < nmid) ? sM[dI[j] * kLdM + dM[m]] : 0.f;
+#pragma unroll
+      for (int m2 = 0; m2 < L2; ++m2)
+        Mmm[m][m2] = (m != m2 && m < nmid && m2 < nmid) ? sM[dM[m] * kLdM + dM[m2]] : 0.f;
+#pragma unroll
+    for (int j = 0; j < L1; ++j)
+#pragma unroll
+      for (int m = 0; m < L2; ++m)
+        Mim[j][m] = (m < nmid) ? sM[dI[j] * kLdM + dM[m]] : 0.f;
+  }
 
   // Outer patterns o = t + T i: the low log2(T) bits of o are the lane's own
   // and fixed, so the lane-bit part of the rest state is built once and each
@@ -280,12 +288,27 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
         const int mb = ctz_c((unsigned)s);
         const bool up = (gray_c((unsigned)s) >> mb) & 1u;
         A = up ? A + gm[mb] : A - gm[mb];
+        if (BLOCKS) {
+          // column mb of the team table: M(inner j, mb) at j, M(mid m, mb) at L1 + m
+          float col[kColStride];
 #pragma unroll
-        for (int m = 0; m < L2; ++m)
-          if (m != mb) gm[m] = up ? gm[m] + Mmm[m][mb] : gm[m] - Mmm[m][mb];
+          for (int e = 0; e < kColStride; e += 4) {
+            const float4 c4 = *reinterpret_cast<const float4*>(colt + mb * kColStride + e);
+            col[e] = c4.x; col[e + 1] = c4.y; col[e + 2] = c4.z; col[e + 3] = c4.w;
+          }
 #pragma unroll
-        for (int j = 0; j < L1; ++j)
-          q[j] = up ? q[j] + Mim[j][mb] : q[j] - Mim[j][mb];
+          for (int m = 0; m < L2; ++m)
+            if (m != mb) gm[m] = up ? gm[m] + col[L1 + m] : gm[m] - col[L1 + m];
+#pragma unroll
+          for (int j = 0; j < L1; ++j) q[j] = up ? q[j] + col[j] : q[j] - col[j];
+        } else {
+#pragma unroll
+          for (int m = 0; m < L2; ++m)
+            if (m != mb) gm[m] = up ? gm[m] + Mmm[m][mb] : gm[m] - Mmm[m][mb];
+#pragma unroll
+          for (int j = 0; j < L1; ++j)
+            q[j] = up ? q[j] + Mim[j][mb] : q[j] - Mim[j][mb];
+        }
       }
       float mbk;
       if (!CLOSED) {
@@ -343,6 +366,29 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
   m1 = best;
   b1 = Sbits | bb;
   m2 = fminf(g2, second);
+}
+
+// Team-cooperative build of the column table (lane lt of T); sync after.
+template <int L1, int L2>
+__device__ __forceinline__ void col_build(const float* sM, const SlotView& sv, int lt, int T,
+                                          float* colt) {
+  const int k = sv.k;
+  const int nmid = min(max(k - L1, 0), L2);
+  for (int e = lt; e < L2 * kColStride; e += T) {
+    const int m = e / kColStride, c = e % kColStride;
+    float v = 0.f;
+    if (m < nmid) {
+      const int dm = sv.dot[L1 + m];
+      if (c < L1) {
+        const int dj = c < k ? sv.dot[c] : 0;
+        v = sM[dj * kLdM + dm];
+      } else if (c < L1 + L2) {
+        const int m2 = c - L1;
+        if (m2 != m && m2 < nmid) v = sM[sv.dot[L1 + m2] * kLdM + dm];
+      }
+    }
+    colt[e] = v;
+  }
 }
 
 // Team-level finish of a block-level search: every lane of the team (lane lt
