@@ -260,23 +260,34 @@ def run_ours(args):
                               "unit counts and max clock; MEASURED_PEAKS.json has no FP32 figure)"}
 
     # ---- end to end: host matrices in, host charge map out ----
+    # Every step uploads the model from host memory (the library stages it
+    # in pinned memory and copies it in stream order), runs the call and
+    # reads the charge map, energies and flags back into pinned host
+    # buffers; two host buffer sets alternate, so the host prepares step k+1
+    # while step k runs, and a set is reused only after its copy has landed.
     Cdd, Cgd = cfg["Cdd"], cfg["Cgd"]
-    hn = torch.empty((P, n_dot), dtype=torch.int8, pin_memory=True)
-    hU = torch.empty(P, dtype=torch.float64, pin_memory=True)
-    hf = torch.empty(P, dtype=torch.uint8, pin_memory=True)
+    ras_c = api.make_raster(ras, Cgd.shape[1])
+    slots = [(torch.empty((P, n_dot), dtype=torch.int8, pin_memory=True),
+              torch.empty(P, dtype=torch.float64, pin_memory=True),
+              torch.empty(P, dtype=torch.uint8, pin_memory=True),
+              torch.cuda.Event()) for _ in range(2)]
     ke = max(3, min(args.steps, 200))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(ke):
-        api.qa_model_update(h, Cdd, Cgd)
-        step()
+    for i in range(ke):
+        hn, hU, hf, done = slots[i % 2]
+        done.synchronize()
+        api.qa_model_update_async(h, Cdd, Cgd, stream)
+        api.qa_ground_state_open(h, ras_c, 1.0, out_n, out_U, out_f, stream)
         hn.copy_(out_n, non_blocking=True)
         hU.copy_(out_U, non_blocking=True)
         hf.copy_(out_f, non_blocking=True)
-        stream.synchronize()
+        done.record(stream)
+    stream.synchronize()
     e2e_s = dist.max_over_ranks((time.perf_counter() - t0) / ke)
+    hn = slots[0][0]
     bi = Cdd.nbytes + Cgd.nbytes + 3 * 8 * Cgd.shape[1] + 4 * 8 + 2 * 4
-    bo = hn.numel() + hU.numel() * 8 + hf.numel()
+    bo = hn.numel() + slots[0][1].numel() * 8 + slots[0][2].numel()
 
     extra = {"paper_context": PAPER_CONTEXT,
              "flagged_per_diagram": st["flagged"], "near_tie": st["near_tie"],

@@ -134,6 +134,15 @@ int qa_model_create(const double* Cdd, const double* Cgd, int n_dot, int n_gate,
  * as at creation); same checks as qa_model_create.  Synchronous. */
 int qa_model_update(qa_model* m, const double* Cdd, const double* Cgd);
 
+/* The same, asynchronously on `stream`: the host checks and the FP64
+ * Cholesky inverse run before the call returns (errors as qa_model_update),
+ * the result is copied from the model's pinned staging buffer to the device
+ * in stream order, so calls on `stream` after it see the new model.  Work on
+ * other streams that reads the model must be ordered by the caller.  A second
+ * update waits for the first one's copy to finish before reusing the staging
+ * buffer. */
+int qa_model_update_async(qa_model* m, const double* Cdd, const double* Cgd, void* stream);
+
 /* Replace the capacitances from DEVICE FP64 Maxwell matrices (same shape) and
  * recompute M = Cdd^-1 by an FP64 Cholesky on the GPU, asynchronously on
  * `stream`.  A Cholesky failure is recorded on the device; the next call that

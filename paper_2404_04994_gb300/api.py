@@ -106,6 +106,7 @@ def load():
     sig = {
         "qa_model_create": (I, [D, D, I, I, I, ctypes.c_double, ctypes.POINTER(P)]),
         "qa_model_update": (I, [P, D, D]),
+        "qa_model_update_async": (I, [P, D, D, P]),
         "qa_model_update_dev": (I, [P, P, P, P]),
         "qa_model_destroy": (I, [P]),
         "qa_model_shape": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I)]),
@@ -194,7 +195,10 @@ def _dev(t, dtype, numel=None, name="buffer"):
 
 def make_raster(r, n_gate):
     """qa_raster from a dict {V0, u, w, x0, x1, y0, y1, W, H}; the struct
-    keeps its host arrays alive."""
+    keeps its host arrays alive.  An existing qa_raster is passed through, so
+    a caller making many calls on one raster can build it once."""
+    if isinstance(r, qa_raster):
+        return r
     V0, pV0 = _host(r["V0"], (n_gate,))
     u, pu = _host(r["u"], (n_gate,))
     w, pw = _host(r["w"], (n_gate,))
@@ -216,6 +220,7 @@ def qa_model_create(Cdd, Cgd, form=QA_FORM_MAXWELL, carrier_sign=1.0):
     h = ctypes.c_void_p()
     _check(load().qa_model_create(pCd, pCg, n, ng, int(form), float(carrier_sign),
                                   ctypes.byref(h)))
+    _SHAPES[h.value] = (n, ng)
     return h
 
 
@@ -224,6 +229,13 @@ def qa_model_update(m, Cdd, Cgd):
     _, pCd = _host(Cdd, (n, n))
     _, pCg = _host(Cgd, (n, ng))
     _check(load().qa_model_update(m, pCd, pCg))
+
+
+def qa_model_update_async(m, Cdd, Cgd, stream=None):
+    n, ng = qa_model_shape(m)
+    _, pCd = _host(Cdd, (n, n))
+    _, pCg = _host(Cgd, (n, ng))
+    _check(load().qa_model_update_async(m, pCd, pCg, _stream(stream)))
 
 
 def qa_model_update_dev(m, Cdd_dev, Cgd_dev, stream=None):
@@ -235,10 +247,17 @@ def qa_model_update_dev(m, Cdd_dev, Cgd_dev, stream=None):
 
 
 def qa_model_destroy(m):
+    _SHAPES.pop(m.value if isinstance(m, ctypes.c_void_p) else m, None)
     _check(load().qa_model_destroy(m))
 
 
+_SHAPES = {}  # model handle -> (n_dot, n_gate), immutable for a model's lifetime
+
+
 def qa_model_shape(m):
+    key = m.value if isinstance(m, ctypes.c_void_p) else m
+    if key in _SHAPES:
+        return _SHAPES[key]
     n = ctypes.c_int()
     ng = ctypes.c_int()
     _check(load().qa_model_shape(m, ctypes.byref(n), ctypes.byref(ng)))

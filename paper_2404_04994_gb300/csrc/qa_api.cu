@@ -107,6 +107,8 @@ struct qa_model {
   qa::BlockCounts* d_bc_prep = nullptr;
   qa::BlockCounts* d_bc_search = nullptr;
   int n_bc_prep = 0, n_bc_search = 0;
+  qa::ModelData* staging = nullptr;   // pinned, for asynchronous updates
+  cudaEvent_t staged = nullptr;       // last copy out of `staging`
 };
 
 namespace {
@@ -639,6 +641,29 @@ int qa_model_update(qa_model* m, const double* Cdd, const double* Cgd) {
   return QA_OK;
 }
 
+int qa_model_update_async(qa_model* m, const double* Cdd, const double* Cgd, void* stream) {
+  if (!m) return fail(QA_ERR_INVALID, "null model");
+  int rc = select_device(m);
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  if (!m->staging) {
+    e = cudaMallocHost(&m->staging, sizeof(qa::ModelData));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->staged, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "staging buffer");
+  } else {
+    e = cudaEventSynchronize(m->staged);  // the previous copy has left the buffer
+    if (e != cudaSuccess) return cuda_fail(e, "staging buffer");
+  }
+  if ((rc = build_model(m->n, m->ng, m->form, Cdd, Cgd, m->staging))) return rc;
+  e = cudaMemcpyAsync(m->d_md, m->staging, sizeof(qa::ModelData), cudaMemcpyHostToDevice,
+                      (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaEventRecord(m->staged, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "model update");
+  m->host = *m->staging;
+  m->host_stale = false;
+  return QA_OK;
+}
+
 int qa_model_update_dev(qa_model* m, const double* Cdd_dev, const double* Cgd_dev,
                         void* stream) {
   if (!m || !Cdd_dev || !Cgd_dev) return fail(QA_ERR_INVALID, "null argument");
@@ -657,6 +682,8 @@ int qa_model_destroy(qa_model* m) {
   cudaDeviceSynchronize();
   if (m->ws) cudaFree(m->ws);
   if (m->d_md) cudaFree(m->d_md);
+  if (m->staging) cudaFreeHost(m->staging);
+  if (m->staged) cudaEventDestroy(m->staged);
   for (cudaEvent_t& e : m->ev)
     if (e) cudaEventDestroy(e);
   delete m;

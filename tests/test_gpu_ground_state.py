@@ -199,3 +199,29 @@ def test_virtual_gate_raster(qa):
     n, U, f, st = _gpu(qa, cfg, raster=ras, closed=False)
     rep = compare(n, U, f, _oracle(cfg, raster=ras, closed=False), cfg["Cdd"], "virtual raster")
     assert rep["comparable"] > 0.95 * 37 * 29
+
+
+def test_async_model_update_in_stream_order(qa):
+    # two models alternated through qa_model_update_async on one stream: each
+    # call sees the model enqueued before it
+    import torch
+    c1, c2 = inputs.chain4(W=40, H=30), inputs.grid16(W=12, H=9)
+    r = np.random.Generator(np.random.PCG64(3))
+    Cdd2 = inputs.chain_cdd(r, 4, nn=(0.05, 0.2))
+    Cgd2 = inputs.dense_cgd(r, 4)
+    m = qa.Model(c1["Cdd"], c1["Cgd"])
+    ref1 = qa.Model(c1["Cdd"], c1["Cgd"]).ground_state_open(c1["raster"])[0].cpu()
+    ref2 = qa.Model(Cdd2, Cgd2).ground_state_open(c1["raster"])[0].cpu()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        outs = []
+        for k in range(6):
+            Cdd, Cgd = (Cdd2, Cgd2) if k % 2 else (c1["Cdd"], c1["Cgd"])
+            qa.qa_model_update_async(m.handle, Cdd, Cgd, s)
+            outs.append(m.ground_state_open(c1["raster"], stream=s)[0])
+    s.synchronize()
+    for k, o in enumerate(outs):
+        assert bool((o.cpu() == (ref2 if k % 2 else ref1)).all())
+    with pytest.raises(qa.QAError):
+        qa.qa_model_update_async(m.handle, -c1["Cdd"], c1["Cgd"], s)
+    m.close()
