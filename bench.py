@@ -383,6 +383,8 @@ def extra_measurements(api, torch, flush, args):
             c = inputs.grid8(kT=kT)
             ms_step = qag.time_grad_step(c, kT, flush=flush)
             out[f"grad_step_ms_grid8_kT{kT:g}"] = ms_step
+            out[f"grad_step_plain_ms_grid8_kT{kT:g}"] = qag.time_grad_step(c, kT, flush=flush,
+                                                                         graph=False)
     except ImportError:
         pass
     return out

@@ -110,11 +110,11 @@ def target_diagram(Cdd, Cgd, raster, kT, t=1.0):
     return out
 
 
-def time_grad_step(cfg, kT, steps=100, flush=None):
+def time_grad_step(cfg, kT, steps=100, flush=None, graph=True):
     """Milliseconds per capacitance-fitting step (100 Adam steps timed end to
-    end on the device, CUDA graph replay)."""
+    end on the device; CUDA graph replay, or plain launches with graph=False)."""
     target = target_diagram(cfg["Cdd_target"], cfg["Cgd_target"], cfg["raster"], kT)
-    fit = CapacitanceFit(cfg["Cdd"], cfg["Cgd"], cfg["raster"], target, kT)
+    fit = CapacitanceFit(cfg["Cdd"], cfg["Cgd"], cfg["raster"], target, kT, graph=graph)
     for _ in range(3):
         fit.step()
     torch.cuda.synchronize()

@@ -531,8 +531,9 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
   const size_t off_bcp = align_up(off_list + sizeof(qa::ListEntry) * (size_t)P, 256);
   const size_t off_recs = align_up(off_bcp + sizeof(qa::BlockCounts) * ((size_t)P + 1), 256);
   const size_t off_part = align_up(off_recs + sizeof(qa::PixRec) * (size_t)P, 256);
-  const size_t total =
-      off_part + (bwd ? sizeof(float) * qa::soft_partials_floats(m->n, P, cfg) : 0);
+  const size_t off_sums =
+      align_up(off_part + (bwd ? sizeof(float) * qa::soft_partials_floats(m->n, P, cfg) : 0), 256);
+  const size_t total = off_sums + (bwd ? sizeof(double) * (size_t)(qa::kMaxDot * qa::kMaxDot + 3 * qa::kMaxDot) : 0);
   if ((rc = ensure_workspace(m, total))) return rc;
   char* ws = (char*)m->ws;
   m->d_cnt = (qa::Counters*)ws;
@@ -580,6 +581,7 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
   a.out_logZ = out_logZ;
   a.grad_mean = grad_mean;
   a.partials = bwd ? (float*)(ws + off_part) : nullptr;
+  a.sums = bwd ? (double*)(ws + off_sums) : nullptr;
   a.dL_dCdd = dCdd;
   a.dL_dCgd = dCgd;
   a.num_sms = m->num_sms;

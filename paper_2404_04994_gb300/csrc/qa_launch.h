@@ -118,6 +118,7 @@ struct SoftLaunch {
   float* out_logZ;
   const float* grad_mean;  // backward input
   float* partials;      // backward scratch: [blocks][2 * L] double-float sums
+  double* sums;         // backward scratch: [L] block partials summed
   double* dL_dCdd;      // backward outputs
   double* dL_dCgd;
   int num_sms;

@@ -337,22 +337,37 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
   }
 }
 
-// Second stage: sum the block partials in fixed order and apply the chain
-// rule through M = Cdd^-1 and c = s Cgd V:
+// Second stage: one block per contribution e sums the block partials --
+// thread j takes blocks j, j + 256, ... in order, then a fixed shared-memory
+// tree -- so the result does not depend on scheduling.
+static __global__ void __launch_bounds__(256) k_soft_reduce(SoftLaunch a, int nblocks) {
+  __shared__ df red[256];
+  const int e = blockIdx.x;
+  const int L = contrib_len(a.n);
+  df acc = {0.f, 0.f};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    const float* pb = a.partials + (size_t)b * 2 * L;
+    acc = df_add(acc, {pb[2 * e], pb[2 * e + 1]});
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int half = blockDim.x / 2; half > 0; half >>= 1) {
+    if ((int)threadIdx.x < half) red[threadIdx.x] = df_add(red[threadIdx.x], red[threadIdx.x + half]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.sums[e] = df_to_double(red[0]);
+}
+
+// Third stage: the chain rule through M = Cdd^-1 and c = s Cgd V:
 //   dL/dCdd = -M (dL/dM) M,  dL/dCgd = s (S0 V0'^T + S1 (dx u)^T + S2 (dy w)^T)
 // with V0' = V0 + x0 u + y0 w and S0, S1, S2 the sums of dc, ix dc, iy dc.
-static __global__ void k_soft_finalize(SoftLaunch a, int nblocks) {
+static __global__ void k_soft_finalize(SoftLaunch a) {
   __shared__ double sG[kMaxDot * kMaxDot];
   __shared__ double sS[3 * kMaxDot];
   const int n = a.n, ng = a.ng;
   const int L = contrib_len(n);
   for (int e = threadIdx.x; e < L; e += blockDim.x) {
-    df acc = {0.f, 0.f};
-    for (int b = 0; b < nblocks; ++b) {
-      const float* pb = a.partials + (size_t)b * 2 * L;
-      acc = df_add(acc, {pb[2 * e], pb[2 * e + 1]});
-    }
-    const double v = df_to_double(acc);
+    const double v = a.sums[e];
     if (e < tri(n)) {
       // e -> (i, j), i <= j
       int i = 0, rem = e;
@@ -405,7 +420,10 @@ static cudaError_t run_soft(const SoftLaunch& a, cudaStream_t st) {
   }
   if (a.ev) cudaEventRecord(a.ev[0], st);
   k_soft<L1, L2, CLOSED, BWD, KMAX><<<grid, kSoftThreads, smem, st>>>(a);
-  if (BWD) k_soft_finalize<<<1, 256, 0, st>>>(a, (int)grid);
+  if (BWD) {
+    k_soft_reduce<<<contrib_len(a.n), 256, 0, st>>>(a, (int)grid);
+    k_soft_finalize<<<1, 256, 0, st>>>(a);
+  }
   if (a.ev) cudaEventRecord(a.ev[1], st);
   return cudaGetLastError();
 }

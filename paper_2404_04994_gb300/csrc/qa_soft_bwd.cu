@@ -9,81 +9,97 @@ cudaError_t launch_soft_backward(const SoftLaunch& a, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// FP64 Cholesky inverse of a device Cdd (model update on the GPU).  One block:
-// thread 0 factors, threads j < n solve for column j of the inverse.
+// FP64 Cholesky inverse of a device Cdd (model update on the GPU).  One block,
+// everything staged in shared memory: warp 0 factors column by column (lane j
+// the pivot, the lanes below it one dot product each), threads j < n solve for
+// column j of the inverse, and the symmetrisation, Cdd 1 and the 1-norm
+// condition number are spread over the block.
 // ---------------------------------------------------------------------------
 __global__ void k_model_update(ModelData* md, int n, int ng, const double* Cdd,
                                const double* Cgd) {
-  __shared__ double L[kMaxDot * kMaxDot];
+  __shared__ double C[kMaxDot * kMaxDot], L[kMaxDot * kMaxDot], Ms[kMaxDot * kMaxDot];
+  __shared__ double rowsum[kMaxDot], colc[kMaxDot], colm[kMaxDot];
   __shared__ int ok;
   const int tid = threadIdx.x;
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
-    md->Cdd[e] = 0.5 * (Cdd[i * n + j] + Cdd[j * n + i]);
+    const double v = 0.5 * (Cdd[i * n + j] + Cdd[j * n + i]);
+    C[e] = v;
+    md->Cdd[e] = v;
+    L[e] = 0.0;
   }
   for (int e = tid; e < n * ng; e += blockDim.x) md->Cgd[e] = Cgd[e];
+  if (tid == 0) ok = 1;
   __syncthreads();
-  if (tid == 0) {
-    ok = 1;
-    for (int j = 0; j < n && ok; ++j) {
-      double d = md->Cdd[j * n + j];
-      for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
-      if (!(d > 0.0)) { ok = 0; break; }
-      const double ljj = sqrt(d);
-      L[j * n + j] = ljj;
-      for (int i = j + 1; i < n; ++i) {
-        double s = md->Cdd[i * n + j];
-        for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
-        L[i * n + j] = s / ljj;
+  if (tid < 32) {
+    for (int j = 0; j < n; ++j) {
+      if (tid == j) {
+        double d = C[j * n + j];
+        for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
+        L[j * n + j] = d > 0.0 ? sqrt(d) : 0.0;
+        if (!(d > 0.0)) ok = 0;
       }
+      __syncwarp();
+      const double ljj = L[j * n + j];
+      if (!(ljj > 0.0)) break;
+      if (tid > j && tid < n) {
+        double t = C[tid * n + j];
+        for (int k = 0; k < j; ++k) t -= L[tid * n + k] * L[j * n + k];
+        L[tid * n + j] = t / ljj;
+      }
+      __syncwarp();
     }
-    md->status = ok ? 0 : 1;
   }
   __syncthreads();
   if (!ok) {
-    if (tid == 0) md->k.model_bad = 1;
+    if (tid == 0) {
+      md->status = 1;
+      md->k.model_bad = 1;
+    }
     return;
   }
   if (tid < n) {
     const int col = tid;
     double z[kMaxDot], y[kMaxDot];
     for (int i = 0; i < n; ++i) {
-      double s = (i == col) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) s -= L[i * n + k] * z[k];
-      z[i] = s / L[i * n + i];
+      double t = (i == col) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) t -= L[i * n + k] * z[k];
+      z[i] = t / L[i * n + i];
     }
     for (int i = n - 1; i >= 0; --i) {
-      double s = z[i];
-      for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * y[k];
-      y[i] = s / L[i * n + i];
+      double t = z[i];
+      for (int k = i + 1; k < n; ++k) t -= L[k * n + i] * y[k];
+      y[i] = t / L[i * n + i];
     }
-    for (int i = 0; i < n; ++i) md->M[i * n + col] = y[i];
+    for (int i = 0; i < n; ++i) Ms[i * n + col] = y[i];
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    md->M[e] = 0.5 * (Ms[i * n + j] + Ms[j * n + i]);
+  }
+  if (tid < n) {
+    double r = 0.0, sc = 0.0, sm = 0.0;
+    for (int j = 0; j < n; ++j) {
+      r += C[tid * n + j];
+      sc += fabs(C[j * n + tid]);
+      sm += fabs(0.5 * (Ms[j * n + tid] + Ms[tid * n + j]));
+    }
+    rowsum[tid] = r;
+    colc[tid] = sc;
+    colm[tid] = sm;
   }
   __syncthreads();
   if (tid == 0) {
-    for (int i = 0; i < n; ++i)
-      for (int j = i + 1; j < n; ++j) {
-        const double s = 0.5 * (md->M[i * n + j] + md->M[j * n + i]);
-        md->M[i * n + j] = md->M[j * n + i] = s;
-      }
     double tot = 0.0, n1c = 0.0, n1m = 0.0;
     for (int i = 0; i < n; ++i) {
-      double r = 0.0;
-      for (int j = 0; j < n; ++j) r += md->Cdd[i * n + j];
-      md->vs[i] = r;
-      tot += r;
+      tot += rowsum[i];
+      n1c = fmax(n1c, colc[i]);
+      n1m = fmax(n1m, colm[i]);
     }
-    for (int i = 0; i < n; ++i) md->vs[i] /= tot;
-    for (int j = 0; j < n; ++j) {
-      double sc = 0.0, sm = 0.0;
-      for (int i = 0; i < n; ++i) {
-        sc += fabs(md->Cdd[i * n + j]);
-        sm += fabs(md->M[i * n + j]);
-      }
-      n1c = fmax(n1c, sc);
-      n1m = fmax(n1m, sm);
-    }
+    for (int i = 0; i < n; ++i) md->vs[i] = rowsum[i] / tot;
     md->cond = n1c * n1m;
+    md->status = 0;
   }
   __syncthreads();
   // FP32 / double-float forms (same definitions as the host set-up)
