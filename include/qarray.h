@@ -181,6 +181,15 @@ int qa_ground_state_closed(qa_model* m, const qa_raster* r, double threshold,
                            int n_charges, int8_t* out_n, double* out_U,
                            uint8_t* out_flags, void* stream);
 
+/* Ground state of an open (closed = 0) or closed (closed = 1, n_charges
+ * carriers) array with an int16 charge map out_n [H, W, n_dot] (DEVICE,
+ * caller-owned), for scans whose charges exceed int8; charges above 32767
+ * saturate and set QA_FLAG_OVERFLOW.  Otherwise as qa_ground_state_open /
+ * qa_ground_state_closed. */
+int qa_ground_state_i16(qa_model* m, const qa_raster* r, double threshold, int closed,
+                        int n_charges, int16_t* out_n, double* out_U, uint8_t* out_flags,
+                        void* stream);
+
 /* Ground state at an arbitrary list of P gate-voltage vectors V_dev (DEVICE,
  * FP64 [P, n_gate]), the random-voltage workload of Sec. VII.  closed = 0/1.
  * Outputs as above with H * W replaced by P. */

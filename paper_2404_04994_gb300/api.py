@@ -121,6 +121,8 @@ def load():
         "qa_virtual_gate_matrix": (I, [P, P, I, I, I, P]),
         "qa_charge_sensor": (I, [P, ctypes.POINTER(qa_raster), P,
                                  ctypes.POINTER(qa_sensor_params), P, P, P, P]),
+        "qa_ground_state_i16": (I, [P, ctypes.POINTER(qa_raster), ctypes.c_double, I, I,
+                                    P, P, P, P]),
         "qa_brute_force_open": (I, [P, ctypes.POINTER(qa_raster), I, P, P, P, P]),
         "qa_brute_force_closed": (I, [P, ctypes.POINTER(qa_raster), I, P, P, P, P]),
         "qa_soft_occupation": (I, [P, ctypes.POINTER(qa_raster), ctypes.c_double,
@@ -284,6 +286,18 @@ def qa_ground_state_open(m, raster, threshold, out_n, out_U=None, out_flags=None
     _check(load().qa_ground_state_open(
         m, ctypes.byref(r), float(threshold), _dev(out_n, torch.int8, P * n, "out_n"),
         _dev(out_U, torch.float64, P, "out_U"),
+        _dev(out_flags, torch.uint8, P, "out_flags"), _stream(stream)))
+
+
+def qa_ground_state_i16(m, raster, threshold, closed, n_charges, out_n, out_U=None,
+                        out_flags=None, stream=None):
+    import torch
+    n, ng = qa_model_shape(m)
+    r = make_raster(raster, ng)
+    P = r.W * r.H
+    _check(load().qa_ground_state_i16(
+        m, ctypes.byref(r), float(threshold), int(bool(closed)), int(n_charges),
+        _dev(out_n, torch.int16, P * n, "out_n"), _dev(out_U, torch.float64, P, "out_U"),
         _dev(out_flags, torch.uint8, P, "out_flags"), _stream(stream)))
 
 
@@ -492,6 +506,15 @@ class Model:
         qa_ground_state_closed(self.handle, raster, threshold, n_charges, n, U, f,
                                stream)
         return n.view(int(raster["H"]), int(raster["W"]), self.n_dot), U, f
+
+    def ground_state_i16(self, raster, threshold=1.0, closed=False, n_charges=0,
+                         energies=True, flags=True, stream=None):
+        import torch
+        H, W = int(raster["H"]), int(raster["W"])
+        _, U, f = self._outs(H * W, energies, flags)
+        n = torch.empty((H, W, self.n_dot), dtype=torch.int16, device="cuda")
+        qa_ground_state_i16(self.handle, raster, threshold, closed, n_charges, n, U, f, stream)
+        return n, U, f
 
     def ground_state_points(self, V, threshold=1.0, closed=False, n_charges=0,
                             energies=True, flags=True, stream=None):

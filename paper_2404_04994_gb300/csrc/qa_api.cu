@@ -432,7 +432,7 @@ int run_brute(qa_model* m, const qa_raster* r, int closed, int bound, int8_t* ou
 
 int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
                      int n_charges, int8_t* out_n, double* out_U,
-                     uint8_t* out_flags, void* stream) {
+                     uint8_t* out_flags, void* stream, int16_t* out_n16 = nullptr) {
   if (!m) return fail(QA_ERR_INVALID, "null model");
   if (!(t >= 0.0 && t <= 1.0)) return fail(QA_ERR_RANGE, "threshold %g outside [0, 1]", t);
   if (closed && (n_charges < 0 || n_charges > 100000))
@@ -440,7 +440,7 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
   qa::Scan sc;
   int rc = make_scan(m, in, &sc);
   if (rc) return rc;
-  if (sc.P > 0 && !out_n) return fail(QA_ERR_INVALID, "null out_n");
+  if (sc.P > 0 && !out_n && !out_n16) return fail(QA_ERR_INVALID, "null out_n");
   if ((rc = select_device(m))) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const long long P = sc.P;
@@ -489,6 +489,7 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
   a.bc_search = m->d_bc_search;
   a.cnt = m->d_cnt;
   a.one.out_n = out_n;
+  a.one.out_n16 = out_n16;
   a.one.out_U = out_U;
   a.one.out_flags = out_flags;
   a.num_sms = m->num_sms;
@@ -746,6 +747,17 @@ int qa_ground_state_closed(qa_model* m, const qa_raster* r, double threshold,
   in.r = r;
   return run_ground_state(m, in, threshold, 1, n_charges, out_n, out_U, out_flags,
                           stream);
+}
+
+int qa_ground_state_i16(qa_model* m, const qa_raster* r, double threshold, int closed,
+                        int n_charges, int16_t* out_n, double* out_U, uint8_t* out_flags,
+                        void* stream) {
+  if (!r) return fail(QA_ERR_INVALID, "null raster");
+  if (!out_n) return fail(QA_ERR_INVALID, "null out_n");
+  ScanIn in;
+  in.r = r;
+  return run_ground_state(m, in, threshold, closed ? 1 : 0, n_charges, nullptr, out_U,
+                          out_flags, stream, out_n);
 }
 
 int qa_ground_state_points(qa_model* m, const double* V_dev, long long P,

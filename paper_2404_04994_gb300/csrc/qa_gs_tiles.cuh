@@ -18,7 +18,20 @@ constexpr int kRecheckThreads = 128;
 constexpr int kResolveThreads = 256;
 constexpr int kCheckL1 = 4, kCheckL2 = 3;  // resolve/recheck split: 2^9 outer states at k = 16
 constexpr unsigned kBcap = 1024;
-constexpr int kTeamFinishMin = 8;  // teams at least this wide finish the winning block together
+constexpr int kTeamFinishMin = 8;
+
+// One charge of the output map: int8 (saturating at 127) or int16 (at
+// 32767) by the array's output width; saturation sets kFlagOverflow.
+__device__ __forceinline__ void store_charge(const ArrayDesc& a, long long idx, int v,
+                                             unsigned& flags) {
+  if (a.out_n16) {
+    if (v > 32767) { v = 32767; flags |= kFlagOverflow; }
+    a.out_n16[idx] = (int16_t)v;
+  } else {
+    if (v > 127) { v = 127; flags |= kFlagOverflow; }
+    a.out_n[idx] = (int8_t)v;
+  }
+}  // teams at least this wide finish the winning block together
 
 // number of k-subsets of size w (k <= 16)
 __device__ __forceinline__ unsigned long long binom(int k, int w) {
@@ -415,10 +428,7 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
       if ((mask >> i) & 1u) ni += (int)((b1 >> __popc(mask & ((1u << i) - 1u))) & 1u);
       const df ri = df_sub({(float)ni, 0.f}, {rec->chi[i], rec->clo[i]});
       u = df_add(u, df_mul(acc, ri));
-      if (j0 == 0) {
-        if (ni > 127) { ni = 127; flags |= kFlagOverflow; }
-        a.out_n[p * n + i] = (int8_t)ni;
-      }
+      if (j0 == 0) store_charge(a, p * n + i, ni, flags);
     }
   }
   for (int off = 1; off < T; off <<= 1) {
@@ -635,8 +645,7 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
       for (int i = 0; i < n; ++i) {
         int ni = rec->base[i];
         if ((mask >> i) & 1u) ni += (int)((bbits >> __popc(mask & ((1u << i) - 1u))) & 1u);
-        if (ni > 127) { ni = 127; flags |= kFlagOverflow; }
-        a.out_n[p * n + i] = (int8_t)ni;
+        store_charge(a, p * n + i, ni, flags);
       }
       if (a.out_U) a.out_U[p] = df_to_double(df_add(ub, best));
       if (a.out_flags) a.out_flags[p] = (uint8_t)flags;
@@ -870,11 +879,7 @@ __device__ inline void recheck_entry(const GsLaunch& L, const ArrayDesc& a, Rech
         for (int j = 0; j < n; ++j) row += a.md->M[i * n + j] * ((double)nst[j] - sc64[j]);
         U += ((double)nst[i] - sc64[i]) * row;
       }
-      for (int i = 0; i < n; ++i) {
-        int v = nst[i];
-        if (v > 127) { v = 127; flags |= kFlagOverflow; }
-        a.out_n[p * n + i] = (int8_t)v;
-      }
+      for (int i = 0; i < n; ++i) store_charge(a, p * n + i, nst[i], flags);
       if (a.out_U) a.out_U[p] = 0.5 * U;
     }
     if (a.out_flags) a.out_flags[p] = (uint8_t)flags;

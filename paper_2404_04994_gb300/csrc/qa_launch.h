@@ -31,6 +31,7 @@ struct ArrayDesc {
   float bx_qp_scale;   // ... per unit of (1 + max|c| + N_hat) for FP32 QP minima
   PixRec* recs;        // scratch [P]
   int8_t* out_n;
+  int16_t* out_n16;    // int16 charge map instead of out_n when non-null
   double* out_U;
   uint8_t* out_flags;
 };

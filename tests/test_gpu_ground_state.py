@@ -225,3 +225,24 @@ def test_async_model_update_in_stream_order(qa):
     with pytest.raises(qa.QAError):
         qa.qa_model_update_async(m.handle, -c1["Cdd"], c1["Cgd"], s)
     m.close()
+
+
+@pytest.mark.parametrize("closed", [False, True])
+def test_int16_maps_for_large_charges(qa, closed):
+    # gate voltages high enough that the charges pass int8: the int16 map is
+    # exact, the int8 map saturates and flags the overflow
+    cfg = inputs.double_dot(W=37, H=23)
+    ras = dict(cfg["raster"], x0=150.0, x1=190.0, y0=140.0, y1=170.0)
+    nh = 320
+    m = qa.Model(cfg["Cdd"], cfg["Cgd"])
+    n16, U16, f16 = m.ground_state_i16(ras, closed=closed, n_charges=nh)
+    n8, U8, f8 = (m.ground_state_closed(ras, nh) if closed else m.ground_state_open(ras))
+    m.close()
+    n16 = n16.cpu().numpy().reshape(-1, 2).astype(np.int64)
+    rec = oracle.ground_state(cfg["Cdd"], cfg["Cgd"], raster=ras, t=1.0, closed=closed,
+                              n_charges=nh)
+    assert n16.max() > 127
+    compare(n16, U16.cpu().numpy(), f16.cpu().numpy(), rec, cfg["Cdd"], "int16 map")
+    assert ((f8.cpu().numpy() & 128) != 0).any()
+    assert not ((f16.cpu().numpy() & 128) != 0).any()
+    np.testing.assert_array_equal(U8.cpu().numpy(), U16.cpu().numpy())
