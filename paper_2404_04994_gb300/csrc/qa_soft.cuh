@@ -38,8 +38,11 @@ struct TeamSlots {
   float ustar_kT;      // U(n*) / kT  (rounded from double-float)
 };
 
+// D(b) = E(b) - E(b*) from the slots that differ from b*: the first-order
+// terms gp / gm of each and the pair terms between them, read from the team's
+// slot-ordered copy of M (Ms[s * KMAX + s2] = M of the dots of slots s, s2).
 template <int KMAX>
-__device__ __forceinline__ float delta_energy(const TeamSlots& ts, const float* sM,
+__device__ __forceinline__ float delta_energy(const TeamSlots& ts, const float* Ms,
                                               unsigned b) {
   const unsigned d = b ^ ts.bstar;
   float D = 0.f;
@@ -47,11 +50,11 @@ __device__ __forceinline__ float delta_energy(const TeamSlots& ts, const float* 
     const int s = __ffs(m) - 1;
     const bool add = (b >> s) & 1u;
     D += add ? ts.gp[s] : ts.gm[s];
-    const float* Mrow = sM + ts.dot[s] * kLdM;
+    const float* row = Ms + s * KMAX;
     for (unsigned q = d & ((1u << s) - 1u); q; q &= q - 1u) {
       const int s2 = __ffs(q) - 1;
       const bool add2 = (b >> s2) & 1u;
-      const float v = Mrow[ts.dot[s2]];
+      const float v = row[s2];
       D += (add == add2) ? v : -v;
     }
   }
@@ -63,6 +66,10 @@ template <int L1, int L2, bool CLOSED, bool BWD, int KMAX>
 __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
   __shared__ ModelConsts cs;
   __shared__ TeamSlots tsm[kSoftThreads / 4 > 0 ? kSoftThreads / 4 : 1];
+  // slot-ordered M per team (teams of >= 4 lanes for KMAX 8, 32 lanes beyond)
+  constexpr int kMaxTeams = kSoftThreads / (KMAX > 8 ? 32 : 4);
+  __shared__ float slotM[kMaxTeams][KMAX * KMAX];
+  __shared__ float sQa[BWD ? kMaxTeams : 1][tri(KMAX) + KMAX + 1];  // Qa, va, sa of a team
   extern __shared__ float s_contrib[];  // BWD: [teams][contrib_len]
   const int n = a.n;
   stage_consts(&a.md->k, &cs);
@@ -130,6 +137,13 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
     ts.w = CLOSED ? w : -1;
   }
   __syncwarp();
+  float* Ms = slotM[team];
+  if (active)
+    for (int e = lt; e < KMAX * KMAX; e += T) {
+      const int s = e / KMAX, s2 = e % KMAX;
+      Ms[e] = (s < ts.k && s2 < ts.k) ? sM[ts.dot[s] * kLdM + ts.dot[s2]] : 0.f;
+    }
+  __syncwarp();
 
   // pass 1: the minimum-energy candidate b*
   float m1 = kInf, m2 = kInf;
@@ -166,8 +180,9 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
       r[j] = (j < n) ? df_sub({(float)nst[j], 0.f}, {ts.chi[j], ts.clo[j]}) : df{0.f, 0.f};
     for (int i = lt; i < n; i += T) {
       df acc = {0.f, 0.f};
-      for (int j = 0; j < n; ++j)
-        acc = df_add(acc, df_mul({sM[i * kLdM + j], sMlo[i * kLdM + j]}, r[j]));
+#pragma unroll
+      for (int j = 0; j < kMaxDot; ++j)
+        if (j < n) acc = df_add(acc, df_mul({sM[i * kLdM + j], sMlo[i * kLdM + j]}, r[j]));
       u = df_add(u, df_mul(acc, r[i]));
       if ((ts.mask >> i) & 1u) {
         const int s = __popc(ts.mask & ((1u << i) - 1u));
@@ -200,7 +215,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
   if (active) {
     for (unsigned b = (unsigned)lt; b < total; b += (unsigned)T) {
       if (CLOSED && __popc(b) != ts.w) continue;
-      const float wgt = expf(-delta_energy<KMAX>(ts, sM, b) * inv_kT);
+      const float wgt = expf(-delta_energy<KMAX>(ts, Ms, b) * inv_kT);
       Z += wgt;
 #pragma unroll
       for (int s = 0; s < KMAX; ++s)
@@ -261,7 +276,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
   if (active) {
     for (unsigned b = (unsigned)lt; b < total; b += (unsigned)T) {
       if (CLOSED && __popc(b) != ts.w) continue;
-      const float wgt = expf(-delta_energy<KMAX>(ts, sM, b) * inv_kT) * invZ;
+      const float wgt = expf(-delta_energy<KMAX>(ts, Ms, b) * inv_kT) * invZ;
       float gn = gbase;
 #pragma unroll
       for (int s = 0; s < KMAX; ++s)
@@ -287,44 +302,49 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
     for (int e = 0; e < tri(KMAX); ++e) Qa[e] += __shfl_xor_sync(kFullS, Qa[e], off);
   }
   // pixel contribution: dM_p = 1/2 [sa r0 r0^T + r0 va^T + va r0^T + Qa],
-  // rho = sa r0 + va, dc_p = -M rho (dot coordinates)
+  // rho = sa r0 + va, dc_p = -M rho (dot coordinates); the team's lanes split
+  // the entries
+  float* q_s = sQa[BWD ? team : 0];
   if (lt == 0) {
-    if (active) {
-      float r0[kMaxDot], vd[kMaxDot];
-      for (int i = 0; i < n; ++i) {
-        const df rr = df_sub({(float)ts.base[i], 0.f}, {ts.chi[i], ts.clo[i]});
-        r0[i] = rr.hi + rr.lo;
-        vd[i] = 0.f;
-      }
 #pragma unroll
-      for (int s = 0; s < KMAX; ++s)
-        if (s < k) vd[ts.dot[s]] = va[s];
-      int e = 0;
-      for (int i = 0; i < n; ++i)
-        for (int j = i; j < n; ++j) {
-          float q = sa * r0[i] * r0[j] + r0[i] * vd[j] + vd[i] * r0[j];
-          my[e++] = 0.5f * q;
-        }
+    for (int e = 0; e < tri(KMAX); ++e) q_s[e] = Qa[e];
 #pragma unroll
-      for (int s = 0; s < KMAX; ++s)
-#pragma unroll
-        for (int s2 = s; s2 < KMAX; ++s2)
-          if (s2 < k) {
-            int i = ts.dot[s], j = ts.dot[s2];  // i <= j (slots in dot order)
-            const int idx = i * n - i * (i - 1) / 2 + (j - i);
-            my[idx] += (s == s2 ? 0.5f : 0.5f) * Qa[s * KMAX - s * (s - 1) / 2 + (s2 - s)];
-          }
-      const int ix = (int)(p % a.sc.W), iy = (int)(p / a.sc.W);
-      for (int i = 0; i < n; ++i) {
-        float dc = 0.f;
-        for (int j = 0; j < n; ++j) dc -= sM[i * kLdM + j] * (sa * r0[j] + vd[j]);
-        my[tri(n) + i] = dc;
-        my[tri(n) + n + i] = dc * (float)ix;
-        my[tri(n) + 2 * n + i] = dc * (float)iy;
-      }
-    } else {
-      for (int e = 0; e < L; ++e) my[e] = 0.f;
+    for (int s = 0; s < KMAX; ++s) q_s[tri(KMAX) + s] = va[s];
+    q_s[tri(KMAX) + KMAX] = sa;
+  }
+  __syncwarp();
+  const unsigned tmask = active ? ts.mask : 0u;
+  auto slot_of = [&](int i) { return __popc(tmask & ((1u << i) - 1u)); };
+  auto r0_of = [&](int i) {
+    const df rr = df_sub({(float)ts.base[i], 0.f}, {ts.chi[i], ts.clo[i]});
+    return rr.hi + rr.lo;
+  };
+  auto vd_of = [&](int i) { return ((tmask >> i) & 1u) ? q_s[tri(KMAX) + slot_of(i)] : 0.f; };
+  const float sa_t = q_s[tri(KMAX) + KMAX];
+  for (int e = lt; e < tri(n); e += T) {
+    if (!active) { my[e] = 0.f; continue; }
+    int i = 0, rem = e;
+    while (rem >= n - i) { rem -= n - i; ++i; }
+    const int j = i + rem;
+    const float ri = r0_of(i), rj = r0_of(j);
+    float q = sa_t * ri * rj + ri * vd_of(j) + vd_of(i) * rj;
+    if (((tmask >> i) & 1u) && ((tmask >> j) & 1u)) {
+      const int s = slot_of(i), s2 = slot_of(j);  // s <= s2: slots in dot order
+      q += q_s[s * KMAX - s * (s - 1) / 2 + (s2 - s)];
     }
+    my[e] = 0.5f * q;
+  }
+  for (int i = lt; i < n; i += T) {
+    if (!active) {
+      my[tri(n) + i] = my[tri(n) + n + i] = my[tri(n) + 2 * n + i] = 0.f;
+      continue;
+    }
+    float dc = 0.f;
+    for (int j = 0; j < n; ++j) dc -= sM[i * kLdM + j] * (sa_t * r0_of(j) + vd_of(j));
+    const int ix = (int)(p % a.sc.W), iy = (int)(p / a.sc.W);
+    my[tri(n) + i] = dc;
+    my[tri(n) + n + i] = dc * (float)ix;
+    my[tri(n) + 2 * n + i] = dc * (float)iy;
   }
   __syncthreads();
   // block sum over teams in fixed order (double-float), one partial per block
