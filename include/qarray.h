@@ -306,6 +306,22 @@ int qa_soft_occupation_backward(qa_model* m, const qa_raster* r, double kT,
                                 const float* grad_mean, double* dL_dCdd,
                                 double* dL_dCgd, void* stream);
 
+/* qa_soft_occupation that also writes, for the backward pass, an opaque
+ * per-pixel context out_ctx (DEVICE, caller-owned, 8 bytes per pixel: the
+ * anchor candidate and the log of the pixel's partition sum relative to it). */
+int qa_soft_occupation_ctx(qa_model* m, const qa_raster* r, double kT, double threshold,
+                           int closed, int n_charges, float* out_mean, float* out_logZ,
+                           void* out_ctx, void* stream);
+
+/* qa_soft_occupation_backward given the forward's <n> (mean) and context
+ * from qa_soft_occupation_ctx with the same model, raster and settings: the
+ * anchor search and the partition sum are not redone.  Same outputs. */
+int qa_soft_occupation_backward_ctx(qa_model* m, const qa_raster* r, double kT,
+                                    double threshold, int closed, int n_charges,
+                                    const float* grad_mean, const float* mean,
+                                    const void* ctx, double* dL_dCdd, double* dL_dCgd,
+                                    void* stream);
+
 /* Record CUDA events around each kernel that later calls on this model
  * enqueue (enable = 1) or stop doing so (0, the default).  The device time of
  * each kernel of the last call is then reported by qa_model_stats.  Events

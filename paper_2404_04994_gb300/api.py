@@ -130,6 +130,11 @@ def load():
         "qa_soft_occupation_backward": (I, [P, ctypes.POINTER(qa_raster),
                                             ctypes.c_double, ctypes.c_double, I, I,
                                             P, P, P, P]),
+        "qa_soft_occupation_ctx": (I, [P, ctypes.POINTER(qa_raster), ctypes.c_double,
+                                       ctypes.c_double, I, I, P, P, P, P]),
+        "qa_soft_occupation_backward_ctx": (I, [P, ctypes.POINTER(qa_raster),
+                                                ctypes.c_double, ctypes.c_double, I, I,
+                                                P, P, P, P, P, P]),
         "qa_model_stats": (I, [P, P, ctypes.POINTER(qa_stats)]),
         "qa_model_set_timing": (I, [P, I]),
         "qa_ground_state_open_static": (I, [P, ctypes.POINTER(qa_raster),
@@ -448,6 +453,34 @@ def qa_soft_occupation_backward(m, raster, kT, threshold, closed, n_charges,
     _check(load().qa_soft_occupation_backward(
         m, ctypes.byref(r), float(kT), float(threshold), int(closed), int(n_charges),
         _dev(grad_mean, torch.float32, P * n, "grad_mean"),
+        _dev(dL_dCdd, torch.float64, n * n, "dL_dCdd"),
+        _dev(dL_dCgd, torch.float64, n * ng, "dL_dCgd"), _stream(stream)))
+
+
+def qa_soft_occupation_ctx(m, raster, kT, threshold, closed, n_charges, out_mean, out_logZ,
+                           out_ctx, stream=None):
+    """out_ctx: CUDA tensor of P * 8 bytes (e.g. int64 [P])."""
+    import torch
+    n, ng = qa_model_shape(m)
+    r = make_raster(raster, ng)
+    P = r.W * r.H
+    _check(load().qa_soft_occupation_ctx(
+        m, ctypes.byref(r), float(kT), float(threshold), int(closed), int(n_charges),
+        _dev(out_mean, torch.float32, P * n, "out_mean"),
+        _dev(out_logZ, torch.float32, P, "out_logZ"),
+        _dev(out_ctx, torch.int64, P, "out_ctx"), _stream(stream)))
+
+
+def qa_soft_occupation_backward_ctx(m, raster, kT, threshold, closed, n_charges, grad_mean,
+                                    mean, ctx, dL_dCdd, dL_dCgd, stream=None):
+    import torch
+    n, ng = qa_model_shape(m)
+    r = make_raster(raster, ng)
+    P = r.W * r.H
+    _check(load().qa_soft_occupation_backward_ctx(
+        m, ctypes.byref(r), float(kT), float(threshold), int(closed), int(n_charges),
+        _dev(grad_mean, torch.float32, P * n, "grad_mean"),
+        _dev(mean, torch.float32, P * n, "mean"), _dev(ctx, torch.int64, P, "ctx"),
         _dev(dL_dCdd, torch.float64, n * n, "dL_dCdd"),
         _dev(dL_dCgd, torch.float64, n * ng, "dL_dCgd"), _stream(stream)))
 

@@ -26,7 +26,9 @@ class SoftOccupation(torch.autograd.Function):
         Cgd_c = Cgd.detach().contiguous()
         api.qa_model_update_dev(handle, Cdd_c, Cgd_c)
         mean = torch.empty((P, n), dtype=torch.float32, device=Cdd.device)
-        api.qa_soft_occupation(handle, raster, kT, t, closed, n_charges, mean, None)
+        pctx = torch.empty(P, dtype=torch.int64, device=Cdd.device)
+        api.qa_soft_occupation_ctx(handle, raster, kT, t, closed, n_charges, mean, None, pctx)
+        ctx.save_for_backward(mean, pctx)
         ctx.handle = handle
         ctx.raster = raster
         ctx.args = (kT, t, closed, n_charges)
@@ -40,8 +42,9 @@ class SoftOccupation(torch.autograd.Function):
         dCdd = torch.empty((n, n), dtype=torch.float64, device=g.device)
         dCgd = torch.empty((n, ng), dtype=torch.float64, device=g.device)
         kT, t, closed, n_charges = ctx.args
-        api.qa_soft_occupation_backward(ctx.handle, ctx.raster, kT, t, closed, n_charges,
-                                        g, dCdd, dCgd)
+        mean, pctx = ctx.saved_tensors
+        api.qa_soft_occupation_backward_ctx(ctx.handle, ctx.raster, kT, t, closed, n_charges,
+                                            g, mean, pctx, dCdd, dCgd)
         return dCdd, dCgd, None, None, None, None, None, None
 
 

@@ -506,7 +506,9 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
 
 int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
              int n_charges, float* out_mean, float* out_logZ,
-             const float* grad_mean, double* dCdd, double* dCgd, void* stream) {
+             const float* grad_mean, double* dCdd, double* dCgd, void* stream,
+             uint2* ctx_out = nullptr, const uint2* ctx_in = nullptr,
+             const float* mean_in = nullptr) {
   const bool bwd = grad_mean != nullptr;
   if (!m) return fail(QA_ERR_INVALID, "null model");
   if (!r) return fail(QA_ERR_INVALID, "null raster");
@@ -581,6 +583,9 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
   a.out_mean = out_mean;
   a.out_logZ = out_logZ;
   a.grad_mean = grad_mean;
+  a.ctx_out = ctx_out;
+  a.ctx_in = ctx_in;
+  a.mean_in = mean_in;
   a.partials = bwd ? (float*)(ws + off_part) : nullptr;
   a.sums = bwd ? (double*)(ws + off_sums) : nullptr;
   a.dL_dCdd = dCdd;
@@ -898,6 +903,24 @@ int qa_soft_occupation_backward(qa_model* m, const qa_raster* r, double kT,
   if (!grad_mean) return fail(QA_ERR_INVALID, "null grad_mean");
   return run_soft(m, r, kT, threshold, closed, n_charges, nullptr, nullptr,
                   grad_mean, dL_dCdd, dL_dCgd, stream);
+}
+
+int qa_soft_occupation_ctx(qa_model* m, const qa_raster* r, double kT, double threshold,
+                           int closed, int n_charges, float* out_mean, float* out_logZ,
+                           void* out_ctx, void* stream) {
+  if (!out_ctx) return fail(QA_ERR_INVALID, "null out_ctx");
+  return run_soft(m, r, kT, threshold, closed, n_charges, out_mean, out_logZ, nullptr,
+                  nullptr, nullptr, stream, (uint2*)out_ctx);
+}
+
+int qa_soft_occupation_backward_ctx(qa_model* m, const qa_raster* r, double kT,
+                                    double threshold, int closed, int n_charges,
+                                    const float* grad_mean, const float* mean,
+                                    const void* ctx, double* dL_dCdd, double* dL_dCgd,
+                                    void* stream) {
+  if (!grad_mean || !mean || !ctx) return fail(QA_ERR_INVALID, "null grad_mean, mean or ctx");
+  return run_soft(m, r, kT, threshold, closed, n_charges, nullptr, nullptr, grad_mean,
+                  dL_dCdd, dL_dCgd, stream, nullptr, (const uint2*)ctx, mean);
 }
 
 int qa_model_stats(qa_model* m, void* stream, qa_stats* out) {

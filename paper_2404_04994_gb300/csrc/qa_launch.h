@@ -118,6 +118,9 @@ struct SoftLaunch {
   float* out_mean;      // forward outputs
   float* out_logZ;
   const float* grad_mean;  // backward input
+  uint2* ctx_out;          // forward, optional: per pixel (b* bits, log sum exp(-D/kT))
+  const uint2* ctx_in;     // backward, optional: the forward's context ...
+  const float* mean_in;    // ... and its <n>, so passes 1 and 2 are not redone
   float* partials;      // backward scratch: [blocks][2 * L] double-float sums
   double* sums;         // backward scratch: [L] block partials summed
   double* dL_dCdd;      // backward outputs

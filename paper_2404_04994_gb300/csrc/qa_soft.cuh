@@ -145,21 +145,26 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
     }
   __syncwarp();
 
-  // pass 1: the minimum-energy candidate b*
+  // pass 1: the minimum-energy candidate b* (from the forward's context when
+  // the backward has it)
+  const bool use_ctx = BWD && a.ctx_in != nullptr;
   float m1 = kInf, m2 = kInf;
   unsigned b1 = 0u;
   unsigned long long ev = 0;
-  if (active) {
+  if (use_ctx) {
+    if (active) b1 = a.ctx_in[p].x;
+  } else if (active) {
     SlotView sv{ts.dot, ts.h, ts.k, ts.w};
     search_lane<L1, L2, CLOSED, false>(sM, sv, lt, T, 0.f, nullptr, nullptr, 0u, m1,
                                        b1, m2, ev);
   }
-  for (int off = 1; off < T; off <<= 1) {
-    const float om1 = __shfl_xor_sync(kFullS, m1, off);
-    const unsigned ob1 = __shfl_xor_sync(kFullS, b1, off);
-    const float om2 = __shfl_xor_sync(kFullS, m2, off);
-    top2_merge(m1, b1, m2, om1, ob1, om2);
-  }
+  if (!use_ctx)
+    for (int off = 1; off < T; off <<= 1) {
+      const float om1 = __shfl_xor_sync(kFullS, m1, off);
+      const unsigned ob1 = __shfl_xor_sync(kFullS, b1, off);
+      const float om2 = __shfl_xor_sync(kFullS, m2, off);
+      top2_merge(m1, b1, m2, om1, ob1, om2);
+    }
   // gradient at b* and U(b*) in double-float; lanes split the rows
   df u = {0.f, 0.f};
   if (active) {
@@ -212,20 +217,24 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
 #pragma unroll
   for (int s = 0; s < KMAX; ++s) acc[s] = 0.f;
   const float inv_kT = 1.0f / kT;
-  if (active) {
-    for (unsigned b = (unsigned)lt; b < total; b += (unsigned)T) {
-      if (CLOSED && __popc(b) != ts.w) continue;
-      const float wgt = expf(-delta_energy<KMAX>(ts, Ms, b) * inv_kT);
-      Z += wgt;
+  if (use_ctx) {
+    if (active) Z = expf(__uint_as_float(a.ctx_in[p].y));
+  } else {
+    if (active) {
+      for (unsigned b = (unsigned)lt; b < total; b += (unsigned)T) {
+        if (CLOSED && __popc(b) != ts.w) continue;
+        const float wgt = expf(-delta_energy<KMAX>(ts, Ms, b) * inv_kT);
+        Z += wgt;
 #pragma unroll
-      for (int s = 0; s < KMAX; ++s)
-        if ((b >> s) & 1u) acc[s] += wgt;
+        for (int s = 0; s < KMAX; ++s)
+          if ((b >> s) & 1u) acc[s] += wgt;
+      }
     }
-  }
-  for (int off = 1; off < T; off <<= 1) {
-    Z += __shfl_xor_sync(kFullS, Z, off);
+    for (int off = 1; off < T; off <<= 1) {
+      Z += __shfl_xor_sync(kFullS, Z, off);
 #pragma unroll
-    for (int s = 0; s < KMAX; ++s) acc[s] += __shfl_xor_sync(kFullS, acc[s], off);
+      for (int s = 0; s < KMAX; ++s) acc[s] += __shfl_xor_sync(kFullS, acc[s], off);
+    }
   }
   if (!BWD) {
     if (active) {
@@ -240,6 +249,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
         a.out_mean[p * n + i] = v;
       }
       if (lt == 0 && a.out_logZ) a.out_logZ[p] = logf(Z) - ts.ustar_kT;
+      if (lt == 0 && a.ctx_out) a.ctx_out[p] = make_uint2(ts.bstar, __float_as_uint(logf(Z)));
     }
     return;
   }
@@ -255,16 +265,18 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
   for (int s = 0; s < KMAX; ++s) gs[s] = 0.f;
   if (active) {
     const float* g = a.grad_mean + p * n;
-    for (int i = 0; i < n; ++i) {
-      gbase += g[i] * (float)ts.base[i];
-      gmean += g[i] * (float)ts.base[i];
+    for (int i = 0; i < n; ++i) gbase += g[i] * (float)ts.base[i];
+    if (use_ctx) {
+      for (int i = 0; i < n; ++i) gmean += g[i] * a.mean_in[p * n + i];
+    } else {
+      gmean = gbase;
+#pragma unroll
+      for (int s = 0; s < KMAX; ++s)
+        if (s < k) gmean += g[ts.dot[s]] * acc[s] * invZ;
     }
 #pragma unroll
     for (int s = 0; s < KMAX; ++s)
-      if (s < k) {
-        gs[s] = g[ts.dot[s]];
-        gmean += gs[s] * acc[s] * invZ;
-      }
+      if (s < k) gs[s] = g[ts.dot[s]];
   }
   float sa = 0.f;
   float va[KMAX];
