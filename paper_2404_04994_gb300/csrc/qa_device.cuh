@@ -201,6 +201,13 @@ __host__ __device__ constexpr int popc_c(unsigned v) {
 }
 
 // 3-input minimum (PTX ISA 8.8+, sm_100+).
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the previous kernel of the stream finishes;
+// it waits here before touching that kernel's results.  The previous kernel
+// lets it start once every block has signalled (or exited).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_signal() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ float fmin3(float a, float b, float c) {
   float d;
   asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));

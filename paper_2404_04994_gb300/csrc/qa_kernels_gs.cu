@@ -9,6 +9,9 @@ template <bool CLOSED>
 __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch L) {
   __shared__ PrepShared sh;
   const ArrayDesc& a = L.one;
+  if (L.prep_zeroes_counters && blockIdx.x == 0)
+    for (int e = threadIdx.x; e < (int)(sizeof(Counters) / sizeof(unsigned)); e += blockDim.x)
+      reinterpret_cast<unsigned*>(L.cnt)[e] = 0u;
   prep_stage_array(a, sh);
   PrepAcc acc;
   const long long team_base = (long long)blockIdx.x * (kPrepThreads / a.prep_team);
@@ -19,6 +22,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch L) {
     o.qp = acc.qp;
     o.doubled = acc.doubled;
   }
+  grid_dep_signal();
 }
 
 template <int L1, int L2, bool CLOSED, bool TF>
@@ -26,6 +30,7 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch L) {
   __shared__ SearchShared sh;
   const ArrayDesc& a = L.one;
   stage_consts(&a.md->k, &sh.cs);
+  grid_dep_wait();  // the records come from k_prep
   __syncthreads();
   SearchAcc acc;
   const long long team_base = (long long)blockIdx.x * (kSearchThreads / a.cfg.T);
@@ -37,12 +42,14 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch L) {
     o.boundary = acc.boundary;
     o.overflow = acc.overflow;
   }
+  grid_dep_signal();
 }
 
 // Near-tie list: one block per entry, grid-stride.  In a batched call the
 // entries belong to different arrays; the model is restaged when it changes.
 __global__ void __launch_bounds__(kResolveThreads) k_resolve(GsLaunch L) {
   __shared__ ResolveShared S;
+  grid_dep_wait();  // the tie list comes from the search
   const unsigned ntie = L.cnt->n_tie;
   int staged = -1;
   unsigned my_res = 0;
@@ -62,11 +69,13 @@ __global__ void __launch_bounds__(kResolveThreads) k_resolve(GsLaunch L) {
     __syncthreads();
   }
   if (threadIdx.x == 0 && my_res) atomicAdd(&L.cnt->resolved, (unsigned long long)my_res);
+  grid_dep_signal();
 }
 
 // FP64 recheck list: one block per entry, grid-stride.
 __global__ void __launch_bounds__(kRecheckThreads) k_recheck(GsLaunch L) {
   __shared__ RecheckShared S;
+  grid_dep_wait();  // the FP64 list is complete once the resolve has run
   const unsigned nflag = L.cnt->n_flag;
   int staged = -1;
   for (unsigned it = blockIdx.x; it < nflag; it += gridDim.x) {
@@ -98,26 +107,51 @@ int search_blocks(const GsLaunch& L) {
   return (int)((L.one.sc.P + teams - 1) / teams);
 }
 
+// Launch with programmatic stream serialisation (the kernel waits for its
+// predecessor's results with grid_dep_wait).
+template <typename... KArgs>
+static cudaError_t launch_dependent(void (*kern)(KArgs...), unsigned grid, unsigned block,
+                                    cudaStream_t st, KArgs... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 cudaError_t launch_lists(const GsLaunch& L, cudaStream_t st) {
-  k_resolve<<<L.num_sms, kResolveThreads, 0, st>>>(L);
-  k_recheck<<<L.num_sms, kRecheckThreads, 0, st>>>(L);
-  return cudaGetLastError();
+  cudaError_t e = launch_dependent(k_resolve, (unsigned)L.num_sms, kResolveThreads, st, L);
+  if (e == cudaSuccess) e = launch_dependent(k_recheck, (unsigned)L.num_sms, kRecheckThreads, st, L);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int L1, int L2, bool CLOSED>
-static cudaError_t run(const GsLaunch& L, cudaStream_t st) {
+static cudaError_t run(const GsLaunch& Lin, cudaStream_t st) {
+  // k_prep clears the counters (no memset node); search, resolve and recheck
+  // start early behind their predecessor (programmatic dependent launch)
+  GsLaunch L = Lin;
+  L.prep_zeroes_counters = 1;
   if (L.ev) cudaEventRecord(L.ev[0], st);
-  cudaMemsetAsync(L.cnt, 0, sizeof(Counters), st);
   k_prep<CLOSED><<<prep_blocks(L), kPrepThreads, 0, st>>>(L);
   if (L.ev) cudaEventRecord(L.ev[1], st);
+  cudaError_t e;
   if (L.one.cfg.T >= kTeamFinishMin)
-    k_search<L1, L2, CLOSED, true><<<search_blocks(L), kSearchThreads, 0, st>>>(L);
+    e = launch_dependent(k_search<L1, L2, CLOSED, true>, (unsigned)search_blocks(L),
+                         kSearchThreads, st, L);
   else
-    k_search<L1, L2, CLOSED, false><<<search_blocks(L), kSearchThreads, 0, st>>>(L);
+    e = launch_dependent(k_search<L1, L2, CLOSED, false>, (unsigned)search_blocks(L),
+                         kSearchThreads, st, L);
+  if (e != cudaSuccess) return e;
   if (L.ev) cudaEventRecord(L.ev[2], st);
-  launch_lists(L, st);
+  e = launch_lists(L, st);
   if (L.ev) cudaEventRecord(L.ev[3], st);
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_prep(const GsLaunch& L, cudaStream_t st) {

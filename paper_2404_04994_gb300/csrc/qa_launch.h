@@ -57,6 +57,7 @@ struct GsLaunch {
   BlockCounts* bc_search;      // scratch [search blocks]
   int grid_prep, grid_search;  // batched call: persistent grid sizes
   int num_sms;
+  int prep_zeroes_counters;  // single-array call: k_prep clears *cnt (no memset)
   cudaEvent_t* ev;     // optional: events around prep / search / resolve+recheck
 };
 
