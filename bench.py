@@ -317,7 +317,8 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": world * P / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)},
-            "gpu_launches": 3 * args.steps, "clocks": clk, "extra": extra}
+            # per step: k_prep, k_search, k_resolve, k_recheck
+            "gpu_launches": 4 * args.steps, "clocks": clk, "extra": extra}
     if rank == 0:
         print(json.dumps(line))
     m.close()
