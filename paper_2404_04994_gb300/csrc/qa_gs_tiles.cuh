@@ -497,6 +497,9 @@ struct ResolveShared {
   unsigned bcnt;
   df rbest[kResolveThreads / 32], rsec[kResolveThreads / 32];
   unsigned rbits[kResolveThreads / 32];
+  unsigned dbits;   // the decision of warp 0, for the whole block
+  int dok;
+  unsigned dflags;
 };
 
 template <bool CLOSED>
@@ -630,28 +633,60 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
   }
   if (lane == 0) { rbest[wid] = best; rsec[wid] = second; rbits[wid] = bbits; }
   __syncthreads();
-  if (tid == 0) {
-    for (int i = 1; i < NW; ++i) merge(rbest[i], rsec[i], rbits[i]);
-    df ub = {0.f, 0.f};
-    for (int i = 0; i < n; ++i) ub = df_add(ub, sui[i]);
+  // warp 0: merge the warps' results, U(base) = sum_i r0_i h_i / 2, decide
+  if (wid == 0) {
+    static_assert(NW <= 32, "one warp merges the warps");
+    best = {kInf, 0.f};
+    second = {kInf, 0.f};
+    bbits = 0xffffffffu;
+    if (lane < NW) { best = rbest[lane]; second = rsec[lane]; bbits = rbits[lane]; }
+    for (int off = 16; off > 0; off >>= 1) {
+      df ob, os;
+      ob.hi = __shfl_xor_sync(kFull, best.hi, off);
+      ob.lo = __shfl_xor_sync(kFull, best.lo, off);
+      os.hi = __shfl_xor_sync(kFull, second.hi, off);
+      os.lo = __shfl_xor_sync(kFull, second.lo, off);
+      merge(ob, os, __shfl_xor_sync(kFull, bbits, off));
+    }
+    df ub = lane < n ? sui[lane] : df{0.f, 0.f};
+    for (int off = 16; off > 0; off >>= 1) {
+      df o;
+      o.hi = __shfl_xor_sync(kFull, ub.hi, off);
+      o.lo = __shfl_xor_sync(kFull, ub.lo, off);
+      ub = df_add(ub, o);
+    }
     ub = df_mul_f(ub, 0.5f);
-    const double gap = df_to_double(second) - df_to_double(best);
-    const double eps = 1e-10 * (1.0 + fabs(df_to_double(ub)));
-    if (!fits || bbits == 0xffffffffu || !(gap > eps)) {
-      const unsigned at = atomicAdd(&L.cnt->n_flag, 1u);
-      L.flag_list[at] = ListEntry{te.array, (int)p, te.m1, 1};
-    } else {
-      unsigned flags = (a.out_flags ? a.out_flags[p] : 0u) | kFlagRechecked;
-      for (int i = 0; i < n; ++i) {
-        int ni = rec->base[i];
-        if ((mask >> i) & 1u) ni += (int)((bbits >> __popc(mask & ((1u << i) - 1u))) & 1u);
-        store_charge(a, p * n + i, ni, flags);
+    if (lane == 0) {
+      const double gap = df_to_double(second) - df_to_double(best);
+      const double eps = 1e-10 * (1.0 + fabs(df_to_double(ub)));
+      const bool ok = fits && bbits != 0xffffffffu && gap > eps;
+      S.dok = ok ? 1 : 0;
+      S.dbits = bbits;
+      S.dflags = 0u;
+      if (!ok) {
+        const unsigned at = atomicAdd(&L.cnt->n_flag, 1u);
+        L.flag_list[at] = ListEntry{te.array, (int)p, te.m1, 1};
+      } else if (a.out_U) {
+        a.out_U[p] = df_to_double(df_add(ub, best));
       }
-      if (a.out_U) a.out_U[p] = df_to_double(df_add(ub, best));
-      if (a.out_flags) a.out_flags[p] = (uint8_t)flags;
+      atomicMax(&L.cnt->shortlist_max, (unsigned long long)nb);
+    }
+  }
+  __syncthreads();
+  // the charges, one dot per thread
+  if (S.dok) {
+    unsigned fl = 0u;
+    if (tid < n) {
+      int ni = rec->base[tid];
+      if ((mask >> tid) & 1u) ni += (int)((S.dbits >> __popc(mask & ((1u << tid) - 1u))) & 1u);
+      store_charge(a, p * n + tid, ni, fl);
+      if (fl) atomicOr(&S.dflags, fl);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      if (a.out_flags) a.out_flags[p] = (uint8_t)(a.out_flags[p] | kFlagRechecked | S.dflags);
       my_res += 1;
     }
-    atomicMax(&L.cnt->shortlist_max, (unsigned long long)nb);
   }
 }
 
