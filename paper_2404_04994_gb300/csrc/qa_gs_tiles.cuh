@@ -406,29 +406,46 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
     }
   }
 
-  // epilogue: n* = base + bits, U(n*) = 1/2 r^T M r in double-float (team
-  // lanes split the rows; no per-thread arrays, so nothing lands in local
-  // memory)
+  // epilogue: n* = base + bits and r = n* - c in double-float, one lane per
+  // dot, kept in the team's slot-table rows (dead after the finish: r.hi in
+  // sh, the bits of r.lo in sdot); then U(n*) = 1/2 r^T M r with the team's
+  // lanes splitting the rows.  A row's products M_ij r_j are summed with
+  // error-free sums of their high parts and plain FP32 sums of the rounding
+  // errors and low-order parts, whose own error is O(u^2) of the row's
+  // magnitude, then renormalised to double-float.
   df u = {0.f, 0.f};
   unsigned flags = 0u;
+  __syncwarp();
+  float* rhi = sh.sh[team];
+  int* rlo = sh.sdot[team];
   if (active) {
-    // rows i split over nc column chunks so that every lane of the team works
+    for (int i = lt; i < n; i += T) {
+      int ni = rec->base[i];
+      if ((mask >> i) & 1u) ni += (int)((b1 >> __popc(mask & ((1u << i) - 1u))) & 1u);
+      const df ri = df_sub({(float)ni, 0.f}, {rec->chi[i], rec->clo[i]});
+      rhi[i] = ri.hi;
+      rlo[i] = __float_as_int(ri.lo);
+      store_charge(a, p * n + i, ni, flags);
+    }
+  }
+  __syncwarp();
+  if (active) {
     const int nc = T >= 2 * n ? T / n : 1;
     const int cw = (n + nc - 1) / nc;
     for (int task = lt; task < n * nc; task += T) {
       const int i = task / nc, j0 = (task % nc) * cw, j1 = min(n, j0 + cw);
-      df acc = {0.f, 0.f};
+      float shi = 0.f, slo = 0.f;
       for (int j = j0; j < j1; ++j) {
-        int nj = rec->base[j];
-        if ((mask >> j) & 1u) nj += (int)((b1 >> __popc(mask & ((1u << j) - 1u))) & 1u);
-        const df rj = df_sub({(float)nj, 0.f}, {rec->chi[j], rec->clo[j]});
-        acc = df_add(acc, df_mul({sM[i * kLdM + j], sMlo[i * kLdM + j]}, rj));
+        const float mh = sM[i * kLdM + j], ml = sMlo[i * kLdM + j];
+        const float xh = rhi[j], xl = __int_as_float(rlo[j]);
+        const df pr = two_prod(mh, xh);
+        const float small = __fmaf_rn(mh, xl, __fmaf_rn(ml, xh, pr.lo));
+        const df sm = two_sum(shi, pr.hi);
+        shi = sm.hi;
+        slo = __fadd_rn(slo, __fadd_rn(sm.lo, small));
       }
-      int ni = rec->base[i];
-      if ((mask >> i) & 1u) ni += (int)((b1 >> __popc(mask & ((1u << i) - 1u))) & 1u);
-      const df ri = df_sub({(float)ni, 0.f}, {rec->chi[i], rec->clo[i]});
-      u = df_add(u, df_mul(acc, ri));
-      if (j0 == 0) store_charge(a, p * n + i, ni, flags);
+      const df acc = fast_two_sum(shi, slo);
+      u = df_add(u, df_mul(acc, {rhi[i], __int_as_float(rlo[i])}));
     }
   }
   for (int off = 1; off < T; off <<= 1) {

@@ -142,34 +142,8 @@ __device__ __forceinline__ float state_from_scratch(const float* sM,
   return A;
 }
 
-// Adds the slots of add_bits to a rest state (A, q, gm).  Each added slot
-// pairs with every set slot of all_bits below it, so adding disjoint slot sets
-// in increasing slot order, with all_bits holding everything below, gives the
-// same state as state_from_scratch of the union (up to summation order: every
-// value is still a sum of at most 2k rounded terms).  M is symmetric, so the
-// middle gradients gm_m = g_m + sum_s M_{m s} come from the same row.
-template <int L1, int L2>
-__device__ __forceinline__ void state_add(const float* sM, const SlotView& sv,
-                                          unsigned all_bits, unsigned add_bits,
-                                          const int* dI, const int* dM,
-                                          float& A, float* q, float* gm) {
-  for (unsigned bits = add_bits; bits; bits &= bits - 1u) {
-    const int s = __ffs(bits) - 1;
-    const int d = sv.dot[s];
-    const float* Mrow = sM + d * kLdM;
-    float add = sv.h[s] + 0.5f * Mrow[d];
-    for (unsigned prev = all_bits & ((1u << s) - 1u); prev; prev &= prev - 1u)
-      add += Mrow[sv.dot[__ffs(prev) - 1]];
-    A += add;
-#pragma unroll
-    for (int j = 0; j < L1; ++j) q[j] += Mrow[dI[j]];
-#pragma unroll
-    for (int m = 0; m < L2; ++m) gm[m] += Mrow[dM[m]];
-  }
-}
-
-// Search of one lane's share.  Lane t of a team of T handles the outer
-// patterns o = t, t + T, ...; results: best energy m1 with its full slot
+// Search of one lane's share.  Lane t of a team of T (a power of two, at
+// most 256) handles the outer patterns o = t, t + T, ...; results: best energy m1 with its full slot
 // pattern b1, and the second-best energy m2 over the lane's candidates.
 // COLLECT: instead, append every (outer, middle) block whose minimum is
 // <= thr to blist (used by the FP64 recheck to shortlist candidates).
@@ -261,14 +235,40 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
   for (int j = 0; j < L1; ++j) qt[j] = qb[j];
 #pragma unroll
   for (int m = 0; m < L2; ++m) gt[m] = gb[m];
+  // The lane-bit slots: their dots and the lane's 0 / 1 weights.  The sums
+  // below run over every lane slot in increasing order with the weight as a
+  // factor (fma(1, x, y) = x + y rounded, fma(0, x, y) = y exactly), so they
+  // round exactly like sums over the lane's set bits alone, but with a trip
+  // count that is the same for every lane of the team: no divergent,
+  // load-dependent chains.
+  constexpr int kLaneBits = 8;  // log2 of the widest team (a 256-thread block)
+  int dO[kLaneBits];
+  float wO[kLaneBits];
+#pragma unroll
+  for (int i = 0; i < kLaneBits; ++i) {
+    const bool live = i < nlb;
+    dO[i] = live ? sv.dot[L1 + L2 + i] : 0;
+    wO[i] = (live && ((t >> i) & 1)) ? 1.f : 0.f;
+  }
   if (niter) {
-    const unsigned lane_bits = (unsigned)t << (L1 + L2);
-    state_add<L1, L2>(sM, sv, lane_bits, lane_bits, dI, dM, At, qt, gt);
+#pragma unroll
+    for (int i = 0; i < kLaneBits; ++i) {
+      if (i < nlb) {
+        const float* Mrow = sM + dO[i] * kLdM;
+        float add = sv.h[L1 + L2 + i] + 0.5f * Mrow[dO[i]];
+#pragma unroll
+        for (int i2 = 0; i2 < i; ++i2) add = fmaf(wO[i2], Mrow[dO[i2]], add);
+        At = fmaf(wO[i], add, At);
+#pragma unroll
+        for (int j = 0; j < L1; ++j) qt[j] = fmaf(wO[i], Mrow[dI[j]], qt[j]);
+#pragma unroll
+        for (int m = 0; m < L2; ++m) gt[m] = fmaf(wO[i], Mrow[dM[m]], gt[m]);
+      }
+    }
   }
 
   for (unsigned it = 0; it < niter; ++it) {
     const unsigned o = (unsigned)t | (it << nlb);
-    const unsigned obits = o << (L1 + L2);
     float A = At;
     float q[L1 > 0 ? L1 : 1];
     float gm[L2 > 0 ? L2 : 1];
@@ -276,7 +276,28 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
     for (int j = 0; j < L1; ++j) q[j] = qt[j];
 #pragma unroll
     for (int m = 0; m < L2; ++m) gm[m] = gt[m];
-    state_add<L1, L2>(sM, sv, obits, (it << nlb) << (L1 + L2), dI, dM, A, q, gm);
+    // the iteration-bit slots (the same for the whole team), each paired
+    // with the lane slots and with the iteration slots below it
+    for (unsigned ib = it; ib; ib &= ib - 1u) {
+      const int ii = __ffs(ib) - 1;
+      const int d = sv.dot[L1 + L2 + nlb + ii];
+      const float* Mrow = sM + d * kLdM;
+      float add = sv.h[L1 + L2 + nlb + ii] + 0.5f * Mrow[d];
+#pragma unroll
+      for (int i = 0; i < kLaneBits; ++i) {
+        if (i < nlb) {  // reloaded here rather than kept live through the walk
+          const float wi = ((t >> i) & 1) ? 1.f : 0.f;
+          add = fmaf(wi, Mrow[sv.dot[L1 + L2 + i]], add);
+        }
+      }
+      for (unsigned prev = it & ((1u << ii) - 1u); prev; prev &= prev - 1u)
+        add += Mrow[sv.dot[L1 + L2 + nlb + __ffs(prev) - 1]];
+      A += add;
+#pragma unroll
+      for (int j = 0; j < L1; ++j) q[j] += Mrow[dI[j]];
+#pragma unroll
+      for (int m = 0; m < L2; ++m) gm[m] += Mrow[dM[m]];
+    }
     const unsigned obase = o << L2;
     const int popo = __popc(o);
 #pragma unroll
@@ -413,17 +434,28 @@ __device__ __forceinline__ void team_finish(const float* __restrict__ sM, const 
   float A = 0.f, q[L1 > 0 ? L1 : 1];
 #pragma unroll
   for (int j = 0; j < L1; ++j) q[j] = 0.f;
+  int dI[L1 > 0 ? L1 : 1];
+#pragma unroll
+  for (int j = 0; j < L1; ++j) dI[j] = j < k ? sv.dot[j] : 0;
   for (int s = lt; s < kMaxDot; s += T) {
     if (!((Sbits >> s) & 1u)) continue;
     const int d = sv.dot[s];
     const float* Mrow = sM + d * kLdM;
     float add = sv.h[s] + 0.5f * Mrow[d];
-    for (unsigned prev = Sbits & ((1u << s) - 1u); prev; prev &= prev - 1u)
-      add += Mrow[sv.dot[__ffs(prev) - 1]];
+    // pairs with the set slots below s in increasing order, as 0 / 1
+    // weighted terms over a fixed range (Sbits has no inner bits): the same
+    // rounding as a loop over the set bits, without a load-dependent chain
+    const unsigned below = Sbits & ((1u << s) - 1u);
+#pragma unroll
+    for (int s2 = L1; s2 < kMaxDot - 1; ++s2) {
+      const bool on = (below >> s2) & 1u;
+      const int d2 = sv.dot[s2];
+      add = fmaf(on ? 1.f : 0.f, Mrow[on ? d2 : d], add);
+    }
     A += add;
 #pragma unroll
     for (int j = 0; j < L1; ++j)
-      if (j < k) q[j] += Mrow[sv.dot[j]];
+      if (j < k) q[j] += Mrow[dI[j]];
   }
   for (int off = 1; off < T; off <<= 1) {
     A += __shfl_xor_sync(tmask, A, off, T);
@@ -445,16 +477,19 @@ __device__ __forceinline__ void team_finish(const float* __restrict__ sM, const 
   unsigned bb = 0xffffffffu;
   for (int b = lt; b < NI; b += T) {
     if (CLOSED && __popc((unsigned)b) != r) continue;
+    // e = A + sum_{j in b} q_j + sum_{l < j in b} M(I_j, I_l), the terms in
+    // increasing order with 0 / 1 weights (no lane-dependent branches)
     float e = A;
     float pb = 0.f;
 #pragma unroll
     for (int j = 0; j < L1; ++j) {
-      if (!((b >> j) & 1)) continue;
-      e += q[j];
-      if (j < k) {
-        const float* Mrow = sM + sv.dot[j] * kLdM;
-        for (int l = 0; l < j; ++l)
-          if ((b >> l) & 1) pb += Mrow[sv.dot[l]];
+      const float wj = ((b >> j) & 1) ? 1.f : 0.f;
+      e = fmaf(wj, q[j], e);
+      const float* Mrow = sM + dI[j] * kLdM;
+#pragma unroll
+      for (int l = 0; l < j; ++l) {
+        const float wl = (((b >> l) & 1) && j < k) ? wj : 0.f;
+        pb = fmaf(wl, Mrow[dI[l]], pb);
       }
     }
     e += pb;
