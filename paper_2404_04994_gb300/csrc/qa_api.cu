@@ -303,7 +303,10 @@ qa::SearchCfg choose_cfg(int n, double t, long long P, int num_sms) {
   else {
     c = {5, 4, 1};
     const int rest = ke - 9;
-    c.T = rest <= 0 ? 1 : (rest >= 5 ? 32 : (1 << rest));
+    // two pixels per warp at most: a 16-lane team halves the per-pixel
+    // set-up, merge and finish per warp against a 32-lane one, and small
+    // rasters are widened below
+    c.T = rest <= 0 ? 1 : (rest >= 4 ? 16 : (1 << rest));
   }
   // spread a small raster over more lanes while each lane keeps >= 2 outer
   // states of work

@@ -31,7 +31,7 @@ __device__ __forceinline__ void store_charge(const ArrayDesc& a, long long idx, 
     if (v > 127) { v = 127; flags |= kFlagOverflow; }
     a.out_n[idx] = (int8_t)v;
   }
-}  // teams at least this wide finish the winning block together
+}
 
 // number of k-subsets of size w (k <= 16)
 __device__ __forceinline__ unsigned long long binom(int k, int w) {
@@ -674,8 +674,10 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
     }
     ub = df_mul_f(ub, 0.5f);
     if (lane == 0) {
-      const double gap = df_to_double(second) - df_to_double(best);
-      const double eps = 1e-10 * (1.0 + fabs(df_to_double(ub)));
+      // exact-tie test in double-float: second - best against
+      // 1e-10 (1 + |U(base)|) (no FP64 instructions on this path)
+      const float gap = second.hi < kInf ? df_add(second, df_neg(best)).hi : kInf;
+      const float eps = 1e-10f * (1.f + fabsf(ub.hi));
       const bool ok = fits && bbits != 0xffffffffu && gap > eps;
       S.dok = ok ? 1 : 0;
       S.dbits = bbits;

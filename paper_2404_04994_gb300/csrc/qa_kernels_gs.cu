@@ -9,6 +9,9 @@ template <bool CLOSED>
 __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch L) {
   __shared__ PrepShared sh;
   const ArrayDesc& a = L.one;
+  // the search may launch now: it stages its constants and then waits for
+  // this grid's results in grid_dep_wait
+  grid_dep_signal();
   if (L.prep_zeroes_counters && blockIdx.x == 0)
     for (int e = threadIdx.x; e < (int)(sizeof(Counters) / sizeof(unsigned)); e += blockDim.x)
       reinterpret_cast<unsigned*>(L.cnt)[e] = 0u;
@@ -22,7 +25,6 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch L) {
     o.qp = acc.qp;
     o.doubled = acc.doubled;
   }
-  grid_dep_signal();
 }
 
 template <int L1, int L2, bool CLOSED, bool TF>
@@ -32,6 +34,10 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch L) {
   stage_consts(&a.md->k, &sh.cs);
   grid_dep_wait();  // the records come from k_prep
   __syncthreads();
+  // every block of this grid is resident or done once all have passed here:
+  // the resolve grid may launch into the slots that free up, stage its
+  // constants and wait for this grid's results
+  grid_dep_signal();
   SearchAcc acc;
   const long long team_base = (long long)blockIdx.x * (kSearchThreads / a.cfg.T);
   search_tile<L1, L2, CLOSED, TF>(L, a, sh, 0, team_base, a.sc.P, acc);
@@ -42,16 +48,20 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch L) {
     o.boundary = acc.boundary;
     o.overflow = acc.overflow;
   }
-  grid_dep_signal();
 }
 
 // Near-tie list: one block per entry, grid-stride.  In a batched call the
 // entries belong to different arrays; the model is restaged when it changes.
 __global__ void __launch_bounds__(kResolveThreads) k_resolve(GsLaunch L) {
   __shared__ ResolveShared S;
-  grid_dep_wait();  // the tie list comes from the search
-  const unsigned ntie = L.cnt->n_tie;
   int staged = -1;
+  if (!L.table) {  // one array: its model is known before the search ends
+    stage_consts(&L.one.md->k, &S.cs);
+    staged = 0;
+  }
+  grid_dep_signal();  // the recheck may launch and stage likewise
+  grid_dep_wait();    // the tie list comes from the search
+  const unsigned ntie = L.cnt->n_tie;
   unsigned my_res = 0;
   for (unsigned it = blockIdx.x; it < ntie; it += gridDim.x) {
     const ListEntry te = L.tie_list[it];
@@ -69,15 +79,18 @@ __global__ void __launch_bounds__(kResolveThreads) k_resolve(GsLaunch L) {
     __syncthreads();
   }
   if (threadIdx.x == 0 && my_res) atomicAdd(&L.cnt->resolved, (unsigned long long)my_res);
-  grid_dep_signal();
 }
 
 // FP64 recheck list: one block per entry, grid-stride.
 __global__ void __launch_bounds__(kRecheckThreads) k_recheck(GsLaunch L) {
   __shared__ RecheckShared S;
+  int staged = -1;
+  if (!L.table) {  // one array: its model is known before the resolve ends
+    for (int e = threadIdx.x; e < kMaxDot * kLdM; e += blockDim.x) S.sM[e] = L.one.md->k.Mhi[e];
+    staged = 0;
+  }
   grid_dep_wait();  // the FP64 list is complete once the resolve has run
   const unsigned nflag = L.cnt->n_flag;
-  int staged = -1;
   for (unsigned it = blockIdx.x; it < nflag; it += gridDim.x) {
     const ListEntry fe = L.flag_list[it];
     const ArrayDesc& a = desc_of(L, fe.array);
