@@ -590,10 +590,13 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
   df best = {kInf, 0.f}, second = {kInf, 0.f};
   unsigned bbits = 0xffffffffu;
   if (fits) {
-    // eight threads per shortlisted candidate: thread `sub` of a group takes
-    // the set slots s with s = sub (mod 8), adding h_s + M_ss / 2 and the
-    // pair terms with the set slots below s; the group then sums its parts
-    constexpr int kSub = 8;
+    // sixteen threads per shortlisted candidate, thread `sub` taking slot
+    // sub when it is set: h_s + M_ss / 2 plus the pair terms with the set
+    // slots below s, over a fixed range of slots with zero terms for the
+    // others (no data-dependent chains); the high parts are summed
+    // error-free, the low parts and rounding errors in plain FP32 (their own
+    // error is O(u^2) of the magnitudes); the group then sums its slots
+    constexpr int kSub = kMaxDot;
     const int sub = tid & (kSub - 1), grp = tid / kSub;
     const unsigned ncand = nb * NI;
     for (unsigned base_idx = 0; base_idx < ncand; base_idx += kResolveThreads / kSub) {
@@ -607,17 +610,22 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
         ok = (bits >> k) == 0u && (!CLOSED || __popc(bits) == w);
       }
       df E = {0.f, 0.f};
-      if (ok)
-        for (unsigned m = bits; m; m &= m - 1u) {
-          const int s = __ffs(m) - 1;
-          if ((s & (kSub - 1)) != sub) continue;
-          const int d = sdot[s];
-          E = df_add(E, shd[s]);
-          for (unsigned q = bits & ((1u << s) - 1u); q; q &= q - 1u) {
-            const int d2i = sdot[__ffs(q) - 1];
-            E = df_add(E, {sM[d * kLdM + d2i], sMlo[d * kLdM + d2i]});
-          }
+      if (ok && ((bits >> sub) & 1u)) {
+        const int d = sdot[sub];
+        const float* Mr = sM + d * kLdM;
+        const float* Ml = sMlo + d * kLdM;
+        const unsigned below = bits & ((1u << sub) - 1u);
+        float hi = shd[sub].hi, lo = shd[sub].lo;
+#pragma unroll
+        for (int s2 = 0; s2 < kMaxDot - 1; ++s2) {
+          const bool on = (below >> s2) & 1u;
+          const int d2 = on ? sdot[s2] : d;
+          const df t = two_sum(hi, on ? Mr[d2] : 0.f);
+          hi = t.hi;
+          lo = __fadd_rn(lo, __fadd_rn(t.lo, on ? Ml[d2] : 0.f));
         }
+        E = two_sum(hi, lo);
+      }
       for (int off = 1; off < kSub; off <<= 1) {
         df o;
         o.hi = __shfl_xor_sync(kFull, E.hi, off, kSub);
@@ -650,46 +658,31 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
   }
   if (lane == 0) { rbest[wid] = best; rsec[wid] = second; rbits[wid] = bbits; }
   __syncthreads();
-  // warp 0: merge the warps' results, U(base) = sum_i r0_i h_i / 2, decide
-  if (wid == 0) {
-    static_assert(NW <= 32, "one warp merges the warps");
-    best = {kInf, 0.f};
-    second = {kInf, 0.f};
-    bbits = 0xffffffffu;
-    if (lane < NW) { best = rbest[lane]; second = rsec[lane]; bbits = rbits[lane]; }
-    for (int off = 16; off > 0; off >>= 1) {
-      df ob, os;
-      ob.hi = __shfl_xor_sync(kFull, best.hi, off);
-      ob.lo = __shfl_xor_sync(kFull, best.lo, off);
-      os.hi = __shfl_xor_sync(kFull, second.hi, off);
-      os.lo = __shfl_xor_sync(kFull, second.lo, off);
-      merge(ob, os, __shfl_xor_sync(kFull, bbits, off));
-    }
-    df ub = lane < n ? sui[lane] : df{0.f, 0.f};
-    for (int off = 16; off > 0; off >>= 1) {
-      df o;
-      o.hi = __shfl_xor_sync(kFull, ub.hi, off);
-      o.lo = __shfl_xor_sync(kFull, ub.lo, off);
-      ub = df_add(ub, o);
-    }
+  // thread 0: merge the warps' results in warp order, U(base) = sum_i
+  // r0_i h_i / 2 in dot order, decide
+  if (tid == 0) {
+    best = rbest[0];
+    second = rsec[0];
+    bbits = rbits[0];
+    for (int w2 = 1; w2 < NW; ++w2) merge(rbest[w2], rsec[w2], rbits[w2]);
+    df ub = {0.f, 0.f};
+    for (int i = 0; i < n; ++i) ub = df_add(ub, sui[i]);
     ub = df_mul_f(ub, 0.5f);
-    if (lane == 0) {
-      // exact-tie test in double-float: second - best against
-      // 1e-10 (1 + |U(base)|) (no FP64 instructions on this path)
-      const float gap = second.hi < kInf ? df_add(second, df_neg(best)).hi : kInf;
-      const float eps = 1e-10f * (1.f + fabsf(ub.hi));
-      const bool ok = fits && bbits != 0xffffffffu && gap > eps;
-      S.dok = ok ? 1 : 0;
-      S.dbits = bbits;
-      S.dflags = 0u;
-      if (!ok) {
-        const unsigned at = atomicAdd(&L.cnt->n_flag, 1u);
-        L.flag_list[at] = ListEntry{te.array, (int)p, te.m1, 1};
-      } else if (a.out_U) {
-        a.out_U[p] = df_to_double(df_add(ub, best));
-      }
-      atomicMax(&L.cnt->shortlist_max, (unsigned long long)nb);
+    // exact-tie test in double-float: second - best against
+    // 1e-10 (1 + |U(base)|) (no FP64 instructions on this path)
+    const float gap = second.hi < kInf ? df_add(second, df_neg(best)).hi : kInf;
+    const float eps = 1e-10f * (1.f + fabsf(ub.hi));
+    const bool ok = fits && bbits != 0xffffffffu && gap > eps;
+    S.dok = ok ? 1 : 0;
+    S.dbits = bbits;
+    S.dflags = 0u;
+    if (!ok) {
+      const unsigned at = atomicAdd(&L.cnt->n_flag, 1u);
+      L.flag_list[at] = ListEntry{te.array, (int)p, te.m1, 1};
+    } else if (a.out_U) {
+      a.out_U[p] = df_to_double(df_add(ub, best));
     }
+    atomicMax(&L.cnt->shortlist_max, (unsigned long long)nb);
   }
   __syncthreads();
   // the charges, one dot per thread
