@@ -271,21 +271,38 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
   }
   if (model_bad) flags |= kFlagUnresolved;
 
-  // h_i = (M (base - c))_i in double-float, r_j gathered from the team
+  // h_i = (M (base - c))_i, r = base - c in double-float staged in the
+  // team's rows of qx / qz (free after the QP); the products' high parts are
+  // summed error-free and their low parts and rounding errors in plain FP32
+  // (error O(u^2) of sum |M_ij r_j|, far below the final rounding of h to FP32)
   const df r = df_sub({(float)base, 0.f}, c);
-  df acc = {0.f, 0.f};
-  for (int j = 0; j < n; ++j) {
-    df rj;
-    rj.hi = __shfl_sync(tmask, r.hi, j, TP);
-    rj.lo = __shfl_sync(tmask, r.lo, j, TP);
-    if (live) acc = df_add(acc, df_mul({sMhi[lt * kLdM + j], sMlo[lt * kLdM + j]}, rj));
+  const int tb0 = threadIdx.x - lt;
+  __syncwarp(tmask);
+  sh.qx[threadIdx.x] = r.hi;
+  sh.qz[threadIdx.x] = r.lo;
+  __syncwarp(tmask);
+  float h = 0.f;
+  if (live) {
+    float shi = 0.f, slo = 0.f;
+    for (int j = 0; j < n; ++j) {
+      const float mh = sMhi[lt * kLdM + j], ml = sMlo[lt * kLdM + j];
+      const float xh = sh.qx[tb0 + j], xl = sh.qz[tb0 + j];
+      const df pr = two_prod(mh, xh);
+      const float small = __fmaf_rn(mh, xl, __fmaf_rn(ml, xh, pr.lo));
+      const df sm = two_sum(shi, pr.hi);
+      shi = sm.hi;
+      slo = __fadd_rn(slo, __fadd_rn(sm.lo, small));
+    }
+    h = shi + slo;
   }
-  const float h = acc.hi + acc.lo;
+  // S_i = |h_i| + M_ii / 2 + sum over the ambiguous j < i of |M_ij| (fixed
+  // range, no divergent loop)
   float Si = 0.f;
   if (live && amb) {
     Si = fabsf(h) + 0.5f * sMhi[lt * kLdM + lt];
-    for (unsigned m2 = mask & ((1u << lt) - 1u); m2; m2 &= m2 - 1u)
-      Si += fabsf(sMhi[lt * kLdM + (__ffs(m2) - 1)]);
+    const unsigned below = mask & ((1u << lt) - 1u);
+    for (int j = 0; j < n; ++j)
+      Si += ((below >> j) & 1u) ? fabsf(sMhi[lt * kLdM + j]) : 0.f;
   }
   const float S = tsum_f(Si);
   const int k = __popc(mask);
@@ -311,13 +328,16 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
     my_doubled = (flags & kFlagDoubled) ? 1u : 0u;
   }
   __syncwarp();
-  const unsigned long long bc = block_sum(my_cand, sh.red64);
-  const unsigned bq = block_sum(my_qp, sh.red32);
-  const unsigned bd = block_sum(my_doubled, sh.red32);
+  // one block sum of the three counts packed in 64 bits: candidates in the
+  // low 32 (a block prepares 128 / TP pixels of at most 2^N candidates with
+  // TP >= N, below 2^20 in all), QP and doubled pixels (<= 128) above
+  const unsigned long long packed = block_sum(
+      my_cand | ((unsigned long long)my_qp << 32) | ((unsigned long long)my_doubled << 48),
+      sh.red64);
   if (threadIdx.x == 0) {
-    tot.candidates += bc;
-    tot.qp += bq;
-    tot.doubled += bd;
+    tot.candidates += packed & 0xffffffffull;
+    tot.qp += (unsigned)((packed >> 32) & 0xffffu);
+    tot.doubled += (unsigned)(packed >> 48);
   }
 }
 
@@ -476,15 +496,18 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
       if (a.out_flags) a.out_flags[p] = (uint8_t)flags;
     }
   }
-  const unsigned long long bev = block_sum(ev, sh.red64);
-  const unsigned bnt = block_sum(my_nt, sh.red32);
-  const unsigned bbd = block_sum(my_bd, sh.red32);
-  const unsigned bov = block_sum(my_ov, sh.red32);
+  // one block sum of the four counts packed in 64 bits: evaluated slots in
+  // the low 32 (at most 128 pixels of 2^16 slots per block, 2^23), near-tie,
+  // recheck and overflow pixels (<= 128 each) in 10 bits apiece above
+  const unsigned long long packed = block_sum(
+      ev | ((unsigned long long)my_nt << 32) | ((unsigned long long)my_bd << 42) |
+          ((unsigned long long)my_ov << 52),
+      sh.red64);
   if (threadIdx.x == 0) {
-    acc.evaluated += bev;
-    acc.near_tie += bnt;
-    acc.boundary += bbd;
-    acc.overflow += bov;
+    acc.evaluated += packed & 0xffffffffull;
+    acc.near_tie += (unsigned)((packed >> 32) & 0x3ffu);
+    acc.boundary += (unsigned)((packed >> 42) & 0x3ffu);
+    acc.overflow += (unsigned)(packed >> 52);
   }
 }
 
