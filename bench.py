@@ -262,32 +262,37 @@ def run_ours(args):
     # ---- end to end: host matrices in, host charge map out ----
     # Every step uploads the model from host memory (the library stages it
     # in pinned memory and copies it in stream order), runs the call and
-    # reads the charge map, energies and flags back into pinned host
-    # buffers; two host buffer sets alternate, so the host prepares step k+1
-    # while step k runs, and a set is reused only after its copy has landed.
+    # reads the charge map, energies and flags back into pinned host memory;
+    # the three outputs sit in one device block, so one copy brings them
+    # back.  Each step is timed with CUDA events from before the upload to
+    # after the read-back has landed, with the L2 flushed between steps
+    # (outside the events) as for the device-resident number; the host
+    # prepares step k + 1 while the flush runs.
     Cdd, Cgd = cfg["Cdd"], cfg["Cgd"]
     ras_c = api.make_raster(ras, Cgd.shape[1])
-    slots = [(torch.empty((P, n_dot), dtype=torch.int8, pin_memory=True),
-              torch.empty(P, dtype=torch.float64, pin_memory=True),
-              torch.empty(P, dtype=torch.uint8, pin_memory=True),
-              torch.cuda.Event()) for _ in range(2)]
+    nb_n, nb_U = P * n_dot, P * 8
+    off_U = (nb_n + 7) // 8 * 8
+    nbytes = off_U + nb_U + P
+    dblk = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    hblk = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d_n = dblk[:nb_n].view(torch.int8).view(P, n_dot)
+    d_U = dblk[off_U:off_U + nb_U].view(torch.float64)
+    d_f = dblk[off_U + nb_U:]
     ke = max(3, min(args.steps, 200))
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(ke)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(ke)]
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
     for i in range(ke):
-        hn, hU, hf, done = slots[i % 2]
-        done.synchronize()
+        flush.zero_()
+        e0[i].record(stream)
         api.qa_model_update_async(h, Cdd, Cgd, stream)
-        api.qa_ground_state_open(h, ras_c, 1.0, out_n, out_U, out_f, stream)
-        hn.copy_(out_n, non_blocking=True)
-        hU.copy_(out_U, non_blocking=True)
-        hf.copy_(out_f, non_blocking=True)
-        done.record(stream)
-    stream.synchronize()
-    e2e_s = dist.max_over_ranks((time.perf_counter() - t0) / ke)
-    hn = slots[0][0]
+        api.qa_ground_state_open(h, ras_c, 1.0, d_n, d_U, d_f, stream)
+        hblk.copy_(dblk, non_blocking=True)
+        e1[i].record(stream)
+    torch.cuda.synchronize()
+    e2e_s = dist.max_over_ranks(sum(x.elapsed_time(y) for x, y in zip(e0, e1)) * 1e-3 / ke)
     bi = Cdd.nbytes + Cgd.nbytes + 3 * 8 * Cgd.shape[1] + 4 * 8 + 2 * 4
-    bo = hn.numel() + slots[0][1].numel() * 8 + slots[0][2].numel()
+    bo = nb_n + nb_U + P
 
     extra = {"paper_context": PAPER_CONTEXT,
              "flagged_per_diagram": st["flagged"], "near_tie": st["near_tie"],
