@@ -530,8 +530,7 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
   cudaStream_t st = (cudaStream_t)stream;
   const long long P = sc.P;
   qa::SearchCfg cfg;
-  if (m->n <= 4) cfg = {4, 0, 4};
-  else if (m->n <= 8) cfg = {5, 4, 8};
+  if (m->n <= 8) cfg = {5, 4, 8};  // the dense form: teams of 8 lanes
   else cfg = {5, 4, 32};
   const size_t off_list = align_up(sizeof(qa::Counters), 256);
   const size_t off_bcp = align_up(off_list + sizeof(qa::ListEntry) * (size_t)P, 256);

@@ -61,111 +61,69 @@ __device__ __forceinline__ float delta_energy(const TeamSlots& ts, const float* 
   return D;
 }
 
-// Soft occupation (forward) and, with BWD, the per-block gradient partials.
-template <int L1, int L2, bool CLOSED, bool BWD, int KMAX>
-__global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
-  __shared__ ModelConsts cs;
-  __shared__ TeamSlots tsm[kSoftThreads / 4 > 0 ? kSoftThreads / 4 : 1];
-  // slot-ordered M per team (teams of >= 4 lanes for KMAX 8, 32 lanes beyond)
-  constexpr int kMaxTeams = kSoftThreads / (KMAX > 8 ? 32 : 4);
-  __shared__ float slotM[kMaxTeams][KMAX * KMAX];
-  __shared__ float sQa[BWD ? kMaxTeams : 1][tri(KMAX) + KMAX + 1];  // Qa, va, sa of a team
-  extern __shared__ float s_contrib[];  // BWD: [teams][contrib_len]
+// Lane 0 of a team: pixel p's record into the team's slots (slot order: the
+// s-th ambiguous dot; h[] reused slot-ordered).  A pixel whose FP32 candidate
+// set may differ from the exact one is prepared again in FP64.
+template <bool CLOSED>
+__device__ inline void soft_setup(const SoftLaunch& a, TeamSlots& ts, long long p) {
   const int n = a.n;
-  stage_consts(&a.md->k, &cs);
-  __syncthreads();
-  const float* sM = cs.Mhi;
-  const float* sMlo = cs.Mlo;
-  const int T = a.cfg.T;  // >= 4
-  const int team = threadIdx.x / T, lt = threadIdx.x % T;
-  const int teams = blockDim.x / T;
-  const long long p = (long long)blockIdx.x * teams + team;
-  const bool active = p < a.sc.P;
-  TeamSlots& ts = tsm[team];
-  const float kT = (float)a.kT;
-
-  if (active && lt == 0) {
-    const PixRec& rec = a.recs[p];
-    unsigned mask = rec.mask;
-    int w = rec.w;
-    if (rec.flags & (kFlagBoundary | kFlagQPCap)) {
-      // the FP32 candidate set may differ from the exact one: redo it in FP64
-      double c[kMaxDot];
-      int base[kMaxDot];
-      unsigned fl = 0u;
-      if (prep_pixel_f64(a.md, n, a.ng, a.sc, a.mt, p, c, base, mask, w, fl) == 0) {
-        for (int i = 0; i < n; ++i) {
-          double h = 0.0;
-          for (int j = 0; j < n; ++j) h += a.md->M[i * n + j] * ((double)base[j] - c[j]);
-          ts.base[i] = base[i];
-          const df cd = df_from_double(c[i]);
-          ts.chi[i] = cd.hi;
-          ts.clo[i] = cd.lo;
-          ts.h[i] = __double2float_rn(h);
-        }
-      } else {
-        mask = rec.mask;
-        w = rec.w;
-        for (int i = 0; i < n; ++i) {
-          ts.base[i] = rec.base[i];
-          ts.chi[i] = rec.chi[i];
-          ts.clo[i] = rec.clo[i];
-          ts.h[i] = rec.h[i];
-        }
-        atomicAdd(&a.cnt->unresolved, 1ull);
+  const PixRec& rec = a.recs[p];
+  unsigned mask = rec.mask;
+  int w = rec.w;
+  if (rec.flags & (kFlagBoundary | kFlagQPCap)) {
+    // the FP32 candidate set may differ from the exact one: redo it in FP64
+    double c[kMaxDot];
+    int base[kMaxDot];
+    unsigned fl = 0u;
+    if (prep_pixel_f64(a.md, n, a.ng, a.sc, a.mt, p, c, base, mask, w, fl) == 0) {
+      for (int i = 0; i < n; ++i) {
+        double h = 0.0;
+        for (int j = 0; j < n; ++j) h += a.md->M[i * n + j] * ((double)base[j] - c[j]);
+        ts.base[i] = base[i];
+        const df cd = df_from_double(c[i]);
+        ts.chi[i] = cd.hi;
+        ts.clo[i] = cd.lo;
+        ts.h[i] = __double2float_rn(h);
       }
     } else {
+      mask = rec.mask;
+      w = rec.w;
       for (int i = 0; i < n; ++i) {
         ts.base[i] = rec.base[i];
         ts.chi[i] = rec.chi[i];
         ts.clo[i] = rec.clo[i];
         ts.h[i] = rec.h[i];
       }
+      atomicAdd(&a.cnt->unresolved, 1ull);
     }
-    // slot order: h of slot s is h of its dot
-    int s = 0;
-    float hs[kMaxDot];
-    for (unsigned m = mask; m; m &= m - 1u) {
-      const int i = __ffs(m) - 1;
-      ts.dot[s] = i;
-      hs[s] = ts.h[i];
-      ++s;
+  } else {
+    for (int i = 0; i < n; ++i) {
+      ts.base[i] = rec.base[i];
+      ts.chi[i] = rec.chi[i];
+      ts.clo[i] = rec.clo[i];
+      ts.h[i] = rec.h[i];
     }
-    for (int q = 0; q < s; ++q) ts.h[q] = hs[q];  // reuse h[] as slot-ordered
-    ts.mask = mask;
-    ts.k = s;
-    ts.w = CLOSED ? w : -1;
   }
-  __syncwarp();
-  float* Ms = slotM[team];
-  if (active)
-    for (int e = lt; e < KMAX * KMAX; e += T) {
-      const int s = e / KMAX, s2 = e % KMAX;
-      Ms[e] = (s < ts.k && s2 < ts.k) ? sM[ts.dot[s] * kLdM + ts.dot[s2]] : 0.f;
-    }
-  __syncwarp();
+  // slot order: h of slot s is h of its dot
+  int s = 0;
+  float hs[kMaxDot];
+  for (unsigned m = mask; m; m &= m - 1u) {
+    const int i = __ffs(m) - 1;
+    ts.dot[s] = i;
+    hs[s] = ts.h[i];
+    ++s;
+  }
+  for (int q = 0; q < s; ++q) ts.h[q] = hs[q];  // reuse h[] as slot-ordered
+  ts.mask = mask;
+  ts.k = s;
+  ts.w = CLOSED ? w : -1;
+}
 
-  // pass 1: the minimum-energy candidate b* (from the forward's context when
-  // the backward has it)
-  const bool use_ctx = BWD && a.ctx_in != nullptr;
-  float m1 = kInf, m2 = kInf;
-  unsigned b1 = 0u;
-  unsigned long long ev = 0;
-  if (use_ctx) {
-    if (active) b1 = a.ctx_in[p].x;
-  } else if (active) {
-    SlotView sv{ts.dot, ts.h, ts.k, ts.w};
-    search_lane<L1, L2, CLOSED, false>(sM, sv, lt, T, 0.f, nullptr, nullptr, 0u, m1,
-                                       b1, m2, ev);
-  }
-  if (!use_ctx)
-    for (int off = 1; off < T; off <<= 1) {
-      const float om1 = __shfl_xor_sync(kFullS, m1, off);
-      const unsigned ob1 = __shfl_xor_sync(kFullS, b1, off);
-      const float om2 = __shfl_xor_sync(kFullS, m2, off);
-      top2_merge(m1, b1, m2, om1, ob1, om2);
-    }
-  // gradient at b* and U(b*) in double-float; lanes split the rows
+// The gradient at b* (gp / gm of every slot) and U(b*) / kT in double-float,
+// the team's lanes splitting the rows; all lanes of the warp call.
+__device__ inline void soft_anchor(const SoftLaunch& a, TeamSlots& ts, const float* sM,
+                                   const float* sMlo, int T, int lt, bool active, unsigned b1) {
+  const int n = a.n;
   df u = {0.f, 0.f};
   if (active) {
     if (lt == 0) ts.bstar = b1;
@@ -208,6 +166,117 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
     ts.ustar_kT = (float)(df_to_double(uk) / a.kT);
   }
   __syncwarp();
+}
+
+// The pixel's gradient contribution from its candidate moments in slot
+// coordinates (q_s: Qa upper triangle, va, sa; see k_soft), the team's lanes
+// splitting the entries into my[], then the block's partial: the teams'
+// contributions summed in a fixed order (double-float), one per block.  All
+// threads of the block call.
+template <int KMAX>
+__device__ inline void soft_contrib(const SoftLaunch& a, const TeamSlots& ts, const float* q_s,
+                                    float* my, const float* s_contrib, const float* sM, int T,
+                                    int lt, int teams, bool active, long long p) {
+  const int n = a.n;
+  const int L = contrib_len(n);
+  const unsigned tmask = active ? ts.mask : 0u;
+  auto slot_of = [&](int i) { return __popc(tmask & ((1u << i) - 1u)); };
+  auto r0_of = [&](int i) {
+    const df rr = df_sub({(float)ts.base[i], 0.f}, {ts.chi[i], ts.clo[i]});
+    return rr.hi + rr.lo;
+  };
+  auto vd_of = [&](int i) { return ((tmask >> i) & 1u) ? q_s[tri(KMAX) + slot_of(i)] : 0.f; };
+  const float sa_t = q_s[tri(KMAX) + KMAX];
+  for (int e = lt; e < tri(n); e += T) {
+    if (!active) { my[e] = 0.f; continue; }
+    int i = 0, rem = e;
+    while (rem >= n - i) { rem -= n - i; ++i; }
+    const int j = i + rem;
+    const float ri = r0_of(i), rj = r0_of(j);
+    float q = sa_t * ri * rj + ri * vd_of(j) + vd_of(i) * rj;
+    if (((tmask >> i) & 1u) && ((tmask >> j) & 1u)) {
+      const int s = slot_of(i), s2 = slot_of(j);  // s <= s2: slots in dot order
+      q += q_s[s * KMAX - s * (s - 1) / 2 + (s2 - s)];
+    }
+    my[e] = 0.5f * q;
+  }
+  for (int i = lt; i < n; i += T) {
+    if (!active) {
+      my[tri(n) + i] = my[tri(n) + n + i] = my[tri(n) + 2 * n + i] = 0.f;
+      continue;
+    }
+    float dc = 0.f;
+    for (int j = 0; j < n; ++j) dc -= sM[i * kLdM + j] * (sa_t * r0_of(j) + vd_of(j));
+    const int ix = (int)(p % a.sc.W), iy = (int)(p / a.sc.W);
+    my[tri(n) + i] = dc;
+    my[tri(n) + n + i] = dc * (float)ix;
+    my[tri(n) + 2 * n + i] = dc * (float)iy;
+  }
+  __syncthreads();
+  // block sum over teams in fixed order (double-float), one partial per block
+  float* out = a.partials + (size_t)blockIdx.x * 2 * L;
+  for (int e = threadIdx.x; e < L; e += blockDim.x) {
+    df sacc = {0.f, 0.f};
+    for (int q = 0; q < teams; ++q) sacc = df_add(sacc, {s_contrib[q * L + e], 0.f});
+    out[2 * e] = sacc.hi;
+    out[2 * e + 1] = sacc.lo;
+  }
+}
+
+// Soft occupation (forward) and, with BWD, the per-block gradient partials.
+template <int L1, int L2, bool CLOSED, bool BWD, int KMAX>
+__global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
+  __shared__ ModelConsts cs;
+  __shared__ TeamSlots tsm[kSoftThreads / 4 > 0 ? kSoftThreads / 4 : 1];
+  // slot-ordered M per team (teams of >= 4 lanes for KMAX 8, 32 lanes beyond)
+  constexpr int kMaxTeams = kSoftThreads / (KMAX > 8 ? 32 : 4);
+  __shared__ float slotM[kMaxTeams][KMAX * KMAX];
+  __shared__ float sQa[BWD ? kMaxTeams : 1][tri(KMAX) + KMAX + 1];  // Qa, va, sa of a team
+  extern __shared__ float s_contrib[];  // BWD: [teams][contrib_len]
+  const int n = a.n;
+  stage_consts(&a.md->k, &cs);
+  __syncthreads();
+  const float* sM = cs.Mhi;
+  const float* sMlo = cs.Mlo;
+  const int T = a.cfg.T;  // >= 4
+  const int team = threadIdx.x / T, lt = threadIdx.x % T;
+  const int teams = blockDim.x / T;
+  const long long p = (long long)blockIdx.x * teams + team;
+  const bool active = p < a.sc.P;
+  TeamSlots& ts = tsm[team];
+  const float kT = (float)a.kT;
+
+  if (active && lt == 0) soft_setup<CLOSED>(a, ts, p);
+  __syncwarp();
+  float* Ms = slotM[team];
+  if (active)
+    for (int e = lt; e < KMAX * KMAX; e += T) {
+      const int s = e / KMAX, s2 = e % KMAX;
+      Ms[e] = (s < ts.k && s2 < ts.k) ? sM[ts.dot[s] * kLdM + ts.dot[s2]] : 0.f;
+    }
+  __syncwarp();
+
+  // pass 1: the minimum-energy candidate b* (from the forward's context when
+  // the backward has it)
+  const bool use_ctx = BWD && a.ctx_in != nullptr;
+  float m1 = kInf, m2 = kInf;
+  unsigned b1 = 0u;
+  unsigned long long ev = 0;
+  if (use_ctx) {
+    if (active) b1 = a.ctx_in[p].x;
+  } else if (active) {
+    SlotView sv{ts.dot, ts.h, ts.k, ts.w};
+    search_lane<L1, L2, CLOSED, false>(sM, sv, lt, T, 0.f, nullptr, nullptr, 0u, m1,
+                                       b1, m2, ev);
+  }
+  if (!use_ctx)
+    for (int off = 1; off < T; off <<= 1) {
+      const float om1 = __shfl_xor_sync(kFullS, m1, off);
+      const unsigned ob1 = __shfl_xor_sync(kFullS, b1, off);
+      const float om2 = __shfl_xor_sync(kFullS, m2, off);
+      top2_merge(m1, b1, m2, om1, ob1, om2);
+    }
+  soft_anchor(a, ts, sM, sMlo, T, lt, active, b1);
 
   // pass 2: Boltzmann weights relative to b*
   const int k = active ? ts.k : 0;
@@ -325,48 +394,322 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
     q_s[tri(KMAX) + KMAX] = sa;
   }
   __syncwarp();
-  const unsigned tmask = active ? ts.mask : 0u;
-  auto slot_of = [&](int i) { return __popc(tmask & ((1u << i) - 1u)); };
-  auto r0_of = [&](int i) {
-    const df rr = df_sub({(float)ts.base[i], 0.f}, {ts.chi[i], ts.clo[i]});
-    return rr.hi + rr.lo;
-  };
-  auto vd_of = [&](int i) { return ((tmask >> i) & 1u) ? q_s[tri(KMAX) + slot_of(i)] : 0.f; };
-  const float sa_t = q_s[tri(KMAX) + KMAX];
-  for (int e = lt; e < tri(n); e += T) {
-    if (!active) { my[e] = 0.f; continue; }
-    int i = 0, rem = e;
-    while (rem >= n - i) { rem -= n - i; ++i; }
-    const int j = i + rem;
-    const float ri = r0_of(i), rj = r0_of(j);
-    float q = sa_t * ri * rj + ri * vd_of(j) + vd_of(i) * rj;
-    if (((tmask >> i) & 1u) && ((tmask >> j) & 1u)) {
-      const int s = slot_of(i), s2 = slot_of(j);  // s <= s2: slots in dot order
-      q += q_s[s * KMAX - s * (s - 1) / 2 + (s2 - s)];
-    }
-    my[e] = 0.5f * q;
+  soft_contrib<KMAX>(a, ts, q_s, my, s_contrib, sM, T, lt, teams, active, p);
+}
+
+// ---------------------------------------------------------------------------
+// Dense soft occupation for arrays of at most 8 dots (k <= 8 ambiguous
+// slots): a team of 8 lanes per pixel, lane t taking the patterns whose
+// slots 5..7 are the bits of t and, for each, the 32 patterns of slots 0..4
+// from a table.  Both passes evaluate a quadratic pseudo-Boolean function
+//   F(d) = sum_{s in d} G_s + sum_{s < s' in d} W_ss'
+// over every pattern d: the lane forms the rest value A = F(d_out) and the
+// inner coefficients q_j = G_j + sum_{o in d_out} W_jo, then F(d) = A +
+// sum_{j in d_in} q_j + Pw[d_in] by doubling, Pw[d_in] the pair terms among
+// the inner slots -- the terms of the per-candidate sums, in another order.
+//   pass 1 (b*): F = E(b) - E(base): G_s = h_s + M_ss / 2, W = M;
+//   pass 2: F = D(d) = E(b* xor d) - E(b*): G_s = gp_s where b* lacks slot s
+//     (adding it) or gm_s where it has it (removing it), W_ss' = sg_s sg_s'
+//     M_ss' with sg_s = +1 / -1 likewise.
+// The weights w(d) = exp(-D(d) / kT) of a lane go through a superset sum over
+// the inner bits, Wz[S] = sum_{d_in contains S} w(d), which yields Z and the
+// moments sum_d w(d) d_S in flip coordinates; with the gradient of the
+// backward, a_b = -(w_b / (kT Z)) (g . n_b - g . <n>) and g . n_b = g . n* +
+// sum_s gam_s d_s (gam_s = sg_s g_s), so that
+//   sum_b a_b d_S = -(1 / (kT Z)) (c0 M(S) + sum_j gam_j M(S u {j})),
+// M(S) = sum_d w(d) d_S, c0 = g . n* - g . <n>, for |S| <= 2; the charge
+// coordinates follow from n_s = n*_s + sg_s d_s.  Per candidate this costs
+// about three adds and an exponential instead of a sum over the slots that
+// differ from b* and a triangle of moment updates.
+// ---------------------------------------------------------------------------
+constexpr int kDenseT = 8;    // lanes per pixel
+constexpr int kDenseIn = 5;   // inner slots: a table of 32 patterns
+constexpr int kDenseMax = 8;  // slots
+
+// F of the 32 inner patterns for the lane's outer pattern tout (slots 5..7).
+// G / sg per slot, Ms the team's slot-ordered M (zero beyond the k slots,
+// where G is kBig so that no pattern using such a slot counts).
+__device__ __forceinline__ void dense_table(const float* G, const float* sg, const float* Ms,
+                                            unsigned tout, float* F) {
+  constexpr int K = kDenseMax, NI = 1 << kDenseIn, NO = K - kDenseIn;
+  float po[NO];
+#pragma unroll
+  for (int i = 0; i < NO; ++i) po[i] = ((tout >> i) & 1u) ? 1.f : 0.f;
+  // rest value and inner coefficients: 0 / 1-weighted sums over the outer
+  // slots in increasing order
+  float A = 0.f;
+  float q[kDenseIn];
+#pragma unroll
+  for (int j = 0; j < kDenseIn; ++j) q[j] = G[j];
+#pragma unroll
+  for (int i = 0; i < NO; ++i) {
+    const int o = kDenseIn + i;
+    float add = G[o];
+#pragma unroll
+    for (int i2 = 0; i2 < i; ++i2)
+      add = fmaf(po[i2], sg[o] * sg[kDenseIn + i2] * Ms[o * K + kDenseIn + i2], add);
+    A = fmaf(po[i], add, A);
+#pragma unroll
+    for (int j = 0; j < kDenseIn; ++j) q[j] = fmaf(po[i], sg[j] * sg[o] * Ms[j * K + o], q[j]);
   }
-  for (int i = lt; i < n; i += T) {
-    if (!active) {
-      my[tri(n) + i] = my[tri(n) + n + i] = my[tri(n) + 2 * n + i] = 0.f;
-      continue;
+  // pair terms among the inner slots
+  float P[NI];
+  P[0] = 0.f;
+#pragma unroll
+  for (int j = 0; j < kDenseIn; ++j) {
+    float Wj[kDenseIn];
+#pragma unroll
+    for (int l = 0; l < j; ++l) Wj[l] = sg[j] * sg[l] * Ms[j * K + l];
+#pragma unroll
+    for (int b = 0; b < (1 << j); ++b) {
+      float r = 0.f;
+#pragma unroll
+      for (int l = 0; l < j; ++l)
+        if ((b >> l) & 1) r += Wj[l];
+      P[b | (1 << j)] = P[b] + r;
     }
-    float dc = 0.f;
-    for (int j = 0; j < n; ++j) dc -= sM[i * kLdM + j] * (sa_t * r0_of(j) + vd_of(j));
-    const int ix = (int)(p % a.sc.W), iy = (int)(p / a.sc.W);
-    my[tri(n) + i] = dc;
-    my[tri(n) + n + i] = dc * (float)ix;
-    my[tri(n) + 2 * n + i] = dc * (float)iy;
   }
+  // doubling over the inner slots, then the pair terms
+  F[0] = A;
+#pragma unroll
+  for (int j = 0; j < kDenseIn; ++j)
+#pragma unroll
+    for (int b = 0; b < (1 << j); ++b) F[b | (1 << j)] = F[b] + q[j];
+#pragma unroll
+  for (int b = 1; b < NI; ++b) F[b] += P[b];
+}
+
+template <bool CLOSED, bool BWD>
+__global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
+  constexpr int K = kDenseMax, NI = 1 << kDenseIn;
+  constexpr int kTeams = kSoftThreads / kDenseT;
+  __shared__ ModelConsts cs;
+  __shared__ TeamSlots tsm[kTeams];
+  __shared__ float slotM[kTeams][K * K];
+  __shared__ float sQa[BWD ? kTeams : 1][tri(K) + K + 1];  // Qa, va, sa of a team
+  extern __shared__ float s_contrib[];                     // BWD: [teams][contrib_len]
+  const int n = a.n;
+  stage_consts(&a.md->k, &cs);
   __syncthreads();
-  // block sum over teams in fixed order (double-float), one partial per block
-  float* out = a.partials + (size_t)blockIdx.x * 2 * L;
-  for (int e = threadIdx.x; e < L; e += blockDim.x) {
-    df sacc = {0.f, 0.f};
-    for (int q = 0; q < teams; ++q) sacc = df_add(sacc, {s_contrib[q * L + e], 0.f});
-    out[2 * e] = sacc.hi;
-    out[2 * e + 1] = sacc.lo;
+  const float* sM = cs.Mhi;
+  const float* sMlo = cs.Mlo;
+  const int T = kDenseT;
+  const int team = threadIdx.x / T, lt = threadIdx.x % T;
+  const long long p = (long long)blockIdx.x * kTeams + team;
+  const bool active = p < a.sc.P;
+  TeamSlots& ts = tsm[team];
+  const float kT = (float)a.kT;
+
+  if (active && lt == 0) soft_setup<CLOSED>(a, ts, p);
+  __syncwarp();
+  float* Ms = slotM[team];
+  if (active)
+    for (int e = lt; e < K * K; e += T) {
+      const int s = e / K, s2 = e % K;
+      Ms[e] = (s < ts.k && s2 < ts.k) ? sM[ts.dot[s] * kLdM + ts.dot[s2]] : 0.f;
+    }
+  __syncwarp();
+  const int k = active ? ts.k : 0;
+  const int kout = k > kDenseIn ? k - kDenseIn : 0;
+  const unsigned tout = (unsigned)lt;                 // the lane's bits of slots 5..7
+  const bool lane_on = active && lt < (1 << kout);
+  const int wcl = (CLOSED && active) ? ts.w : 0;
+
+  // pass 1: b* (from the forward's context when the backward has it)
+  const bool use_ctx = BWD && a.ctx_in != nullptr;
+  unsigned b1 = 0u;
+  if (use_ctx) {
+    if (active) b1 = a.ctx_in[p].x;
+  } else {
+    float G[K], sg[K], F[NI];
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      G[s] = s < k ? ts.h[s] + 0.5f * Ms[s * K + s] : kBig;
+      sg[s] = 1.f;
+    }
+    dense_table(G, sg, Ms, tout, F);
+    float e1 = kInf, e2 = kInf;
+    unsigned bb = 0u;
+    if (lane_on) {
+      const int pout = __popc(tout);
+#pragma unroll
+      for (int b = 0; b < NI; ++b) {
+        if (CLOSED && popc_c((unsigned)b) + pout != wcl) continue;
+        if (F[b] < e1) { e1 = F[b]; bb = (unsigned)b; }
+      }
+    }
+    b1 = bb | (tout << kDenseIn);
+    for (int off = 1; off < T; off <<= 1) {
+      const float o1 = __shfl_xor_sync(kFullS, e1, off);
+      const unsigned ob = __shfl_xor_sync(kFullS, b1, off);
+      const float o2 = __shfl_xor_sync(kFullS, e2, off);
+      top2_merge(e1, b1, e2, o1, ob, o2);
+    }
   }
+  soft_anchor(a, ts, sM, sMlo, T, lt, active, b1);
+
+  // pass 2: weights relative to b*, superset sums over the inner bits
+  const unsigned bst = active ? ts.bstar : 0u;
+  float w[NI];
+  float sgn[K];
+  {
+    float G[K];
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      const bool has = (bst >> s) & 1u;
+      G[s] = s < k ? (has ? ts.gm[s] : ts.gp[s]) : kBig;
+      sgn[s] = has ? -1.f : 1.f;
+    }
+    dense_table(G, sgn, Ms, tout, w);
+  }
+  const float c2 = -1.4426950408889634f / kT;  // exp(-D / kT) = 2^(c2 D)
+  {
+    const unsigned bst_in = bst & (unsigned)(NI - 1), bst_out = bst >> kDenseIn;
+    const int r_need = wcl - __popc(bst_out ^ tout);
+#pragma unroll
+    for (int b = 0; b < NI; ++b) {
+      const bool ok = lane_on && (!CLOSED || __popc(bst_in ^ (unsigned)b) == r_need);
+      w[b] = ok ? exp2f(c2 * w[b]) : 0.f;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kDenseIn; ++j)
+#pragma unroll
+    for (int b = 0; b < NI; ++b)
+      if (!((b >> j) & 1)) w[b] += w[b | (1 << j)];
+  // the lane's outer slots present (1) or absent (0)
+  float po[K - kDenseIn];
+#pragma unroll
+  for (int i = 0; i < K - kDenseIn; ++i) po[i] = (lane_on && ((tout >> i) & 1u)) ? 1.f : 0.f;
+
+  // Z and the first moments in flip coordinates, summed over the team
+  float Z = w[0];
+  float md[K];
+#pragma unroll
+  for (int s = 0; s < K; ++s) md[s] = s < kDenseIn ? w[1 << s] : po[s - kDenseIn] * w[0];
+  for (int off = 1; off < T; off <<= 1) {
+    Z += __shfl_xor_sync(kFullS, Z, off);
+#pragma unroll
+    for (int s = 0; s < K; ++s) md[s] += __shfl_xor_sync(kFullS, md[s], off);
+  }
+  // sum_b w_b b_s (the weight of slot s taking its +1): Z - md where b* has s
+  float accb[K];
+#pragma unroll
+  for (int s = 0; s < K; ++s) accb[s] = ((bst >> s) & 1u) ? Z - md[s] : md[s];
+  if (!BWD) {
+    if (active) {
+      for (int i = lt; i < n; i += T) {
+        float v = (float)ts.base[i];
+        if ((ts.mask >> i) & 1u) {
+          const int s = __popc(ts.mask & ((1u << i) - 1u));
+#pragma unroll
+          for (int q = 0; q < K; ++q)
+            if (q == s) v += accb[q] / Z;
+        }
+        a.out_mean[p * n + i] = v;
+      }
+      if (lt == 0 && a.out_logZ) a.out_logZ[p] = logf(Z) - ts.ustar_kT;
+      if (lt == 0 && a.ctx_out) a.ctx_out[p] = make_uint2(ts.bstar, __float_as_uint(logf(Z)));
+    }
+    return;
+  }
+
+  // ---- backward: the moments of a_b in flip coordinates, per lane ----
+  float gs[K];
+  float gbase = 0.f, gmean = 0.f;
+#pragma unroll
+  for (int s = 0; s < K; ++s) gs[s] = 0.f;
+  if (active) {
+    const float* g = a.grad_mean + p * n;
+    for (int i = 0; i < n; ++i) gbase += g[i] * (float)ts.base[i];
+    if (use_ctx) {
+      for (int i = 0; i < n; ++i) gmean += g[i] * a.mean_in[p * n + i];
+    } else {
+      gmean = gbase;
+#pragma unroll
+      for (int s = 0; s < K; ++s)
+        if (s < k) gmean += g[ts.dot[s]] * accb[s] / Z;
+    }
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+      if (s < k) gs[s] = g[ts.dot[s]];
+  }
+  // g . n* - g . <n> and the flip-coordinate gradient gam_s = sg_s g_s
+  float c0 = gbase - gmean;
+  float gam[K];
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    if ((bst >> s) & 1u) c0 += gs[s];
+    gam[s] = sgn[s] * gs[s];
+  }
+  // M(S) of the lane: its outer slots of S present, and the superset sum of
+  // the inner ones
+  auto Mx = [&](unsigned S) -> float {
+    float v = w[S & (unsigned)(NI - 1)];
+#pragma unroll
+    for (int i = 0; i < K - kDenseIn; ++i)
+      if ((S >> (kDenseIn + i)) & 1u) v *= po[i];
+    return v;
+  };
+  float sa = c0 * Mx(0u);
+#pragma unroll
+  for (int j = 0; j < K; ++j) sa = fmaf(gam[j], Mx(1u << j), sa);
+  float vd[K];
+#pragma unroll
+  for (int s = 0; s < K; ++s) {
+    float v = c0 * Mx(1u << s);
+#pragma unroll
+    for (int j = 0; j < K; ++j) v = fmaf(gam[j], Mx((1u << s) | (1u << j)), v);
+    vd[s] = v;
+  }
+  float Qd[tri(K - 1)];  // s < s2: index s * (2K - s - 1) / 2 + (s2 - s - 1)
+#pragma unroll
+  for (int s = 0; s < K; ++s)
+#pragma unroll
+    for (int s2 = s + 1; s2 < K; ++s2) {
+      const unsigned S = (1u << s) | (1u << s2);
+      float v = c0 * Mx(S);
+#pragma unroll
+      for (int j = 0; j < K; ++j) v = fmaf(gam[j], Mx(S | (1u << j)), v);
+      Qd[s * (2 * K - s - 1) / 2 + (s2 - s - 1)] = v;
+    }
+  for (int off = 1; off < T; off <<= 1) {
+    sa += __shfl_xor_sync(kFullS, sa, off);
+#pragma unroll
+    for (int s = 0; s < K; ++s) vd[s] += __shfl_xor_sync(kFullS, vd[s], off);
+#pragma unroll
+    for (int e = 0; e < tri(K - 1); ++e) Qd[e] += __shfl_xor_sync(kFullS, Qd[e], off);
+  }
+  // scale by -1 / (kT Z) and turn to charge coordinates, n_s = n*_s + sg_s d_s:
+  //   va_s = bt_s sa + sg_s vd_s,  Qa_ss = va_s,
+  //   Qa_ss' = bt_s bt_s' sa + bt_s sg_s' vd_s' + bt_s' sg_s vd_s + sg_s sg_s' Qd_ss'
+  const float alpha = active ? -1.0f / (kT * Z) : 0.f;
+  float* q_s = sQa[BWD ? team : 0];
+  if (lt == 0) {
+    const float sa_a = alpha * sa;
+    float va[K], vda[K], bt[K];
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      bt[s] = ((bst >> s) & 1u) ? 1.f : 0.f;
+      vda[s] = alpha * vd[s];
+      va[s] = bt[s] * sa_a + sgn[s] * vda[s];
+    }
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      q_s[s * K - s * (s - 1) / 2] = va[s];
+#pragma unroll
+      for (int s2 = s + 1; s2 < K; ++s2)
+        q_s[s * K - s * (s - 1) / 2 + (s2 - s)] =
+            bt[s] * bt[s2] * sa_a + bt[s] * sgn[s2] * vda[s2] + bt[s2] * sgn[s] * vda[s] +
+            sgn[s] * sgn[s2] * alpha * Qd[s * (2 * K - s - 1) / 2 + (s2 - s - 1)];
+      q_s[tri(K) + s] = va[s];
+    }
+    q_s[tri(K) + K] = sa_a;
+  }
+  __syncwarp();
+  const int L = contrib_len(n);
+  float* my = s_contrib + team * L;
+  soft_contrib<K>(a, ts, q_s, my, s_contrib, sM, T, lt, kTeams, active, p);
 }
 
 // Second stage: one block per contribution e sums the block partials --
@@ -460,15 +803,31 @@ static cudaError_t run_soft(const SoftLaunch& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Dense form (up to 8 dots; teams of kDenseT lanes, the host sizes the
+// partials for cfg.T = kDenseT).
+template <bool CLOSED, bool BWD>
+static cudaError_t run_soft_dense(const SoftLaunch& a, cudaStream_t st) {
+  constexpr int teams = kSoftThreads / kDenseT;
+  const long long P = a.sc.P;
+  const unsigned grid = (unsigned)((P + teams - 1) / teams);
+  const size_t smem = BWD ? (size_t)teams * contrib_len(a.n) * sizeof(float) : 0;
+  if (a.ev) cudaEventRecord(a.ev[0], st);
+  k_soft_dense<CLOSED, BWD><<<grid, kSoftThreads, smem, st>>>(a);
+  if (BWD) {
+    k_soft_reduce<<<contrib_len(a.n), 256, 0, st>>>(a, (int)grid);
+    k_soft_finalize<<<1, 256, 0, st>>>(a);
+  }
+  if (a.ev) cudaEventRecord(a.ev[1], st);
+  return cudaGetLastError();
+}
+
 template <bool BWD>
 static cudaError_t dispatch_soft(const SoftLaunch& a, cudaStream_t st) {
-  // The search here only locates b*, so two splits suffice: (4, 0) for up
-  // to four dots and (5, 4) beyond (any k works with either).
+  // up to 8 dots: the dense form; beyond, the per-candidate form, whose
+  // search only locates b*
   const bool cl = a.mt.closed != 0;
-  if (a.n <= 4)
-    return cl ? run_soft<4, 0, true, BWD, 8>(a, st) : run_soft<4, 0, false, BWD, 8>(a, st);
-  if (a.n <= 8)
-    return cl ? run_soft<5, 4, true, BWD, 8>(a, st) : run_soft<5, 4, false, BWD, 8>(a, st);
+  if (a.n <= kDenseMax)
+    return cl ? run_soft_dense<true, BWD>(a, st) : run_soft_dense<false, BWD>(a, st);
   return cl ? run_soft<5, 4, true, BWD, 16>(a, st) : run_soft<5, 4, false, BWD, 16>(a, st);
 }
 

@@ -45,6 +45,35 @@ def test_soft_chain4(qa, closed, t):
         np.testing.assert_allclose(mean.sum(1), 4.0, atol=1e-5)
 
 
+def _chain6():
+    """6-dot chain: 6 ambiguous slots at t = 1, so only two of a team's
+    eight lanes hold outer patterns in the dense form."""
+    r = np.random.Generator(np.random.PCG64(606))
+    Cdd = inputs.chain_cdd(r, 6)
+    Cgd = inputs.dense_cgd(r, 6, off=(0.0, 0.15), decay=0.6)
+    ras = inputs.raster(6, 2, 3, inputs.offsets(r, 6, (2, 3), 0.5, 2.5), W=23, H=19)
+    return {"Cdd": Cdd, "Cgd": Cgd, "raster": ras}
+
+
+@pytest.mark.parametrize("closed", [False, True])
+def test_soft_and_gradient_six_dots(qa, closed):
+    cfg = _chain6()
+    kT, nc = 0.02, 6
+    mean, logZ = _soft_gpu(qa, cfg, kT, closed=closed, n_charges=nc)
+    om, ol = oracle.soft(cfg["Cdd"], cfg["Cgd"], raster=cfg["raster"], kT=kT, closed=closed,
+                         n_charges=nc)
+    assert np.abs(mean - om).max() <= MEAN_TOL
+    rel = np.abs(logZ - ol) / np.maximum(1.0, np.abs(ol))
+    assert rel.max() <= 1e-5, rel.max()
+    gbar = np.random.Generator(np.random.PCG64(7)).normal(size=(23 * 19, 6))
+    dC, dG = _grad_gpu(qa, cfg, kT, gbar, closed=closed, n_charges=nc)
+    _, oC, oG = oracle.soft_grad(cfg["Cdd"], cfg["Cgd"], gbar, raster=cfg["raster"], kT=kT,
+                                 closed=closed, n_charges=nc)
+    sc = max(np.abs(oC).max(), np.abs(oG).max())
+    assert np.abs(dC - oC).max() <= GRAD_RTOL * sc
+    assert np.abs(dG - oG).max() <= GRAD_RTOL * sc
+
+
 def test_soft_sixteen_dots_small(qa):
     cfg = inputs.grid16(W=6, H=5)
     kT = 0.05
