@@ -109,6 +109,18 @@ struct qa_model {
   int n_bc_prep = 0, n_bc_search = 0;
   qa::ModelData* staging = nullptr;   // pinned, for asynchronous updates
   cudaEvent_t staged = nullptr;       // last copy out of `staging`
+  // Model generation (bumped by every update) and the key of the records the
+  // last soft-occupation prep left in the workspace: a backward with the
+  // forward's context on the same model, raster and method reuses them.
+  unsigned long long gen = 0;
+  struct {
+    bool valid;
+    const void* recs;
+    qa::Scan sc;
+    double t;
+    int closed, n_charges;
+    unsigned long long gen;
+  } soft_recs = {};
 };
 
 namespace {
@@ -272,6 +284,7 @@ int ensure_workspace(qa_model* m, size_t bytes) {
   if (m->ws) cudaFree(m->ws);
   m->ws = nullptr;
   m->ws_bytes = 0;
+  m->soft_recs.valid = false;
   const size_t want = bytes + bytes / 2 + (1u << 20);
   e = cudaMalloc(&m->ws, want);
   if (e != cudaSuccess) return fail(QA_ERR_NOMEM, "workspace of %zu bytes: %s", want, cudaGetErrorString(e));
@@ -457,6 +470,7 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
   const size_t total = off_recs + sizeof(qa::PixRec) * Pn;
   if ((rc = ensure_workspace(m, total))) return rc;
   char* ws = (char*)m->ws;
+  m->soft_recs.valid = false;  // this call's records replace any soft prep's
   m->d_cnt = (qa::Counters*)ws;
   m->last_P = P;
   m->n_bc_prep = m->n_bc_search = 0;
@@ -567,9 +581,24 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
   g.cnt = m->d_cnt;
   g.num_sms = m->num_sms;
   if (m->timing) cudaEventRecord(m->ev[0], st);
-  m->n_bc_prep = qa::prep_blocks(g);
-  e = qa::launch_prep(g, st);
-  if (e != cudaSuccess) return cuda_fail(e, "prep launch");
+  // the backward with the forward's context skips the prep when the records
+  // of that forward (same model generation, raster and method) are in place
+  const bool same_recs = m->soft_recs.valid && m->soft_recs.recs == (const void*)g.one.recs &&
+                         std::memcmp(&m->soft_recs.sc, &sc, sizeof(sc)) == 0 &&
+                         m->soft_recs.t == t && m->soft_recs.closed == (closed ? 1 : 0) &&
+                         m->soft_recs.n_charges == g.one.mt.n_charges && m->soft_recs.gen == m->gen;
+  if (!(bwd && ctx_in && same_recs)) {
+    m->n_bc_prep = qa::prep_blocks(g);
+    e = qa::launch_prep(g, st);
+    if (e != cudaSuccess) return cuda_fail(e, "prep launch");
+    m->soft_recs.valid = true;
+    m->soft_recs.recs = g.one.recs;
+    m->soft_recs.sc = sc;
+    m->soft_recs.t = t;
+    m->soft_recs.closed = closed ? 1 : 0;
+    m->soft_recs.n_charges = g.one.mt.n_charges;
+    m->soft_recs.gen = m->gen;
+  }
 
   qa::SoftLaunch a;
   std::memset(&a, 0, sizeof(a));
@@ -648,6 +677,7 @@ int qa_model_update(qa_model* m, const double* Cdd, const double* Cgd) {
   if (e != cudaSuccess) return cuda_fail(e, "model update");
   m->host = md;
   m->host_stale = false;
+  ++m->gen;
   return QA_OK;
 }
 
@@ -671,6 +701,7 @@ int qa_model_update_async(qa_model* m, const double* Cdd, const double* Cgd, voi
   if (e != cudaSuccess) return cuda_fail(e, "model update");
   m->host = *m->staging;
   m->host_stale = false;
+  ++m->gen;
   return QA_OK;
 }
 
@@ -683,6 +714,7 @@ int qa_model_update_dev(qa_model* m, const double* Cdd_dev, const double* Cgd_de
                                           (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "model update launch");
   m->host_stale = true;
+  ++m->gen;
   return QA_OK;
 }
 

@@ -11,14 +11,15 @@ cudaError_t launch_soft_backward(const SoftLaunch& a, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // FP64 Cholesky inverse of a device Cdd (model update on the GPU).  One block,
 // everything staged in shared memory: warp 0 factors column by column (lane j
-// the pivot, the lanes below it one dot product each), threads j < n solve for
-// column j of the inverse, and the symmetrisation, Cdd 1 and the 1-norm
+// the pivot, the lanes below it one dot product each; the pivot's reciprocal
+// once, products after), threads j < n solve for column j of the inverse, and the symmetrisation, Cdd 1 and the 1-norm
 // condition number are spread over the block.
 // ---------------------------------------------------------------------------
 __global__ void k_model_update(ModelData* md, int n, int ng, const double* Cdd,
                                const double* Cgd) {
   __shared__ double C[kMaxDot * kMaxDot], L[kMaxDot * kMaxDot], Ms[kMaxDot * kMaxDot];
   __shared__ double rowsum[kMaxDot], colc[kMaxDot], colm[kMaxDot];
+  __shared__ double inv_diag[kMaxDot];  // 1 / L_jj: one FP64 division per column
   __shared__ int ok;
   const int tid = threadIdx.x;
   for (int e = tid; e < n * n; e += blockDim.x) {
@@ -36,16 +37,18 @@ __global__ void k_model_update(ModelData* md, int n, int ng, const double* Cdd,
       if (tid == j) {
         double d = C[j * n + j];
         for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
-        L[j * n + j] = d > 0.0 ? sqrt(d) : 0.0;
+        const double ljj = d > 0.0 ? sqrt(d) : 0.0;
+        L[j * n + j] = ljj;
+        inv_diag[j] = d > 0.0 ? 1.0 / ljj : 0.0;
         if (!(d > 0.0)) ok = 0;
       }
       __syncwarp();
-      const double ljj = L[j * n + j];
-      if (!(ljj > 0.0)) break;
+      if (!(L[j * n + j] > 0.0)) break;
+      const double rjj = inv_diag[j];
       if (tid > j && tid < n) {
         double t = C[tid * n + j];
         for (int k = 0; k < j; ++k) t -= L[tid * n + k] * L[j * n + k];
-        L[tid * n + j] = t / ljj;
+        L[tid * n + j] = t * rjj;
       }
       __syncwarp();
     }
@@ -64,12 +67,12 @@ __global__ void k_model_update(ModelData* md, int n, int ng, const double* Cdd,
     for (int i = 0; i < n; ++i) {
       double t = (i == col) ? 1.0 : 0.0;
       for (int k = 0; k < i; ++k) t -= L[i * n + k] * z[k];
-      z[i] = t / L[i * n + i];
+      z[i] = t * inv_diag[i];
     }
     for (int i = n - 1; i >= 0; --i) {
       double t = z[i];
       for (int k = i + 1; k < n; ++k) t -= L[k * n + i] * y[k];
-      y[i] = t / L[i * n + i];
+      y[i] = t * inv_diag[i];
     }
     for (int i = 0; i < n; ++i) Ms[i * n + col] = y[i];
   }
