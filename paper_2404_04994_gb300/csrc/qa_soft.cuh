@@ -121,15 +121,16 @@ __device__ inline void soft_setup(const SoftLaunch& a, TeamSlots& ts, long long 
 
 // The gradient at b* (gp / gm of every slot) and U(b*) / kT in double-float,
 // the team's lanes splitting the rows; all lanes of the warp call.
+template <int ND>  // dots at most (the arrays below are unrolled to ND)
 __device__ inline void soft_anchor(const SoftLaunch& a, TeamSlots& ts, const float* sM,
                                    const float* sMlo, int T, int lt, bool active, unsigned b1) {
   const int n = a.n;
   df u = {0.f, 0.f};
   if (active) {
     if (lt == 0) ts.bstar = b1;
-    int nst[kMaxDot];
+    int nst[ND];
 #pragma unroll
-    for (int i = 0; i < kMaxDot; ++i) {
+    for (int i = 0; i < ND; ++i) {
       int v = 0;
       if (i < n) {
         v = ts.base[i];
@@ -137,16 +138,18 @@ __device__ inline void soft_anchor(const SoftLaunch& a, TeamSlots& ts, const flo
       }
       nst[i] = v;
     }
-    df r[kMaxDot];
+    df r[ND];
 #pragma unroll
-    for (int j = 0; j < kMaxDot; ++j)
+    for (int j = 0; j < ND; ++j)
       r[j] = (j < n) ? df_sub({(float)nst[j], 0.f}, {ts.chi[j], ts.clo[j]}) : df{0.f, 0.f};
     for (int i = lt; i < n; i += T) {
       df acc = {0.f, 0.f};
 #pragma unroll
-      for (int j = 0; j < kMaxDot; ++j)
+      for (int j = 0; j < ND; ++j)
         if (j < n) acc = df_add(acc, df_mul({sM[i * kLdM + j], sMlo[i * kLdM + j]}, r[j]));
-      u = df_add(u, df_mul(acc, r[i]));
+      int ni = ts.base[i];
+      if ((ts.mask >> i) & 1u) ni += (int)((b1 >> __popc(ts.mask & ((1u << i) - 1u))) & 1u);
+      u = df_add(u, df_mul(acc, df_sub({(float)ni, 0.f}, {ts.chi[i], ts.clo[i]})));
       if ((ts.mask >> i) & 1u) {
         const int s = __popc(ts.mask & ((1u << i) - 1u));
         const float half = 0.5f * sM[i * kLdM + i];
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
       const float om2 = __shfl_xor_sync(kFullS, m2, off);
       top2_merge(m1, b1, m2, om1, ob1, om2);
     }
-  soft_anchor(a, ts, sM, sMlo, T, lt, active, b1);
+  soft_anchor<kMaxDot>(a, ts, sM, sMlo, T, lt, active, b1);
 
   // pass 2: Boltzmann weights relative to b*
   const int k = active ? ts.k : 0;
@@ -546,7 +549,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
       top2_merge(e1, b1, e2, o1, ob, o2);
     }
   }
-  soft_anchor(a, ts, sM, sMlo, T, lt, active, b1);
+  soft_anchor<kDenseMax>(a, ts, sM, sMlo, T, lt, active, b1);
 
   // pass 2: weights relative to b*, superset sums over the inner bits
   const unsigned bst = active ? ts.bstar : 0u;
