@@ -177,26 +177,36 @@ __device__ inline void soft_anchor(const SoftLaunch& a, TeamSlots& ts, const flo
 // contributions summed in a fixed order (double-float), one per block.  All
 // threads of the block call.
 template <int KMAX>
-__device__ inline void soft_contrib(const SoftLaunch& a, const TeamSlots& ts, const float* q_s,
+__device__ inline void soft_contrib(const SoftLaunch& a, TeamSlots& ts, const float* q_s,
                                     float* my, const float* s_contrib, const float* sM, int T,
                                     int lt, int teams, bool active, long long p) {
   const int n = a.n;
   const int L = contrib_len(n);
   const unsigned tmask = active ? ts.mask : 0u;
   auto slot_of = [&](int i) { return __popc(tmask & ((1u << i) - 1u)); };
-  auto r0_of = [&](int i) {
-    const df rr = df_sub({(float)ts.base[i], 0.f}, {ts.chi[i], ts.clo[i]});
-    return rr.hi + rr.lo;
-  };
-  auto vd_of = [&](int i) { return ((tmask >> i) & 1u) ? q_s[tri(KMAX) + slot_of(i)] : 0.f; };
   const float sa_t = q_s[tri(KMAX) + KMAX];
+  // per dot, in the team's rows that are dead by now: r0_i = base_i - c_i,
+  // va_i (charge coordinates, dot order) and rho_i = sa r0_i + va_i
+  float* r0 = ts.gp;
+  float* vd = ts.h;
+  float* rho = ts.gm;
+  if (active)
+    for (int i = lt; i < n; i += T) {
+      const df rr = df_sub({(float)ts.base[i], 0.f}, {ts.chi[i], ts.clo[i]});
+      const float ri = rr.hi + rr.lo;
+      const float vi = ((tmask >> i) & 1u) ? q_s[tri(KMAX) + slot_of(i)] : 0.f;
+      r0[i] = ri;
+      vd[i] = vi;
+      rho[i] = sa_t * ri + vi;
+    }
+  __syncwarp();
+  // dM_ij = 1/2 (r0_i rho_j + va_i r0_j + Qa_ij)
   for (int e = lt; e < tri(n); e += T) {
     if (!active) { my[e] = 0.f; continue; }
     int i = 0, rem = e;
     while (rem >= n - i) { rem -= n - i; ++i; }
     const int j = i + rem;
-    const float ri = r0_of(i), rj = r0_of(j);
-    float q = sa_t * ri * rj + ri * vd_of(j) + vd_of(i) * rj;
+    float q = r0[i] * rho[j] + vd[i] * r0[j];
     if (((tmask >> i) & 1u) && ((tmask >> j) & 1u)) {
       const int s = slot_of(i), s2 = slot_of(j);  // s <= s2: slots in dot order
       q += q_s[s * KMAX - s * (s - 1) / 2 + (s2 - s)];
@@ -209,7 +219,7 @@ __device__ inline void soft_contrib(const SoftLaunch& a, const TeamSlots& ts, co
       continue;
     }
     float dc = 0.f;
-    for (int j = 0; j < n; ++j) dc -= sM[i * kLdM + j] * (sa_t * r0_of(j) + vd_of(j));
+    for (int j = 0; j < n; ++j) dc -= sM[i * kLdM + j] * rho[j];
     const int ix = (int)(p % a.sc.W), iy = (int)(p / a.sc.W);
     my[tri(n) + i] = dc;
     my[tri(n) + n + i] = dc * (float)ix;
@@ -490,6 +500,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
   __shared__ TeamSlots tsm[kTeams];
   __shared__ float slotM[kTeams][K * K];
   __shared__ float sQa[BWD ? kTeams : 1][tri(K) + K + 1];  // Qa, va, sa of a team
+  __shared__ float sQd[BWD ? kTeams : 1][1 + K + tri(K - 1)];  // the same in flip coordinates
   extern __shared__ float s_contrib[];                     // BWD: [teams][contrib_len]
   const int n = a.n;
   stage_consts(&a.md->k, &cs);
@@ -654,18 +665,29 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
       if ((S >> (kDenseIn + i)) & 1u) v *= po[i];
     return v;
   };
-  float sa = c0 * Mx(0u);
+  // each moment summed over the team as soon as it is formed (few live
+  // accumulators), kept by lane 0 in the team's row of sQd: sa, vd[K], then
+  // Qd[s < s2] at s * (2K - s - 1) / 2 + (s2 - s - 1)
+  float* qd = sQd[team];
+  auto team_sum = [&](float v) {
+    for (int off = 1; off < T; off <<= 1) v += __shfl_xor_sync(kFullS, v, off);
+    return v;
+  };
+  {
+    float v = c0 * Mx(0u);
 #pragma unroll
-  for (int j = 0; j < K; ++j) sa = fmaf(gam[j], Mx(1u << j), sa);
-  float vd[K];
+    for (int j = 0; j < K; ++j) v = fmaf(gam[j], Mx(1u << j), v);
+    v = team_sum(v);
+    if (lt == 0) qd[0] = v;
+  }
 #pragma unroll
   for (int s = 0; s < K; ++s) {
     float v = c0 * Mx(1u << s);
 #pragma unroll
     for (int j = 0; j < K; ++j) v = fmaf(gam[j], Mx((1u << s) | (1u << j)), v);
-    vd[s] = v;
+    v = team_sum(v);
+    if (lt == 0) qd[1 + s] = v;
   }
-  float Qd[tri(K - 1)];  // s < s2: index s * (2K - s - 1) / 2 + (s2 - s - 1)
 #pragma unroll
   for (int s = 0; s < K; ++s)
 #pragma unroll
@@ -674,38 +696,31 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
       float v = c0 * Mx(S);
 #pragma unroll
       for (int j = 0; j < K; ++j) v = fmaf(gam[j], Mx(S | (1u << j)), v);
-      Qd[s * (2 * K - s - 1) / 2 + (s2 - s - 1)] = v;
+      v = team_sum(v);
+      if (lt == 0) qd[1 + K + s * (2 * K - s - 1) / 2 + (s2 - s - 1)] = v;
     }
-  for (int off = 1; off < T; off <<= 1) {
-    sa += __shfl_xor_sync(kFullS, sa, off);
-#pragma unroll
-    for (int s = 0; s < K; ++s) vd[s] += __shfl_xor_sync(kFullS, vd[s], off);
-#pragma unroll
-    for (int e = 0; e < tri(K - 1); ++e) Qd[e] += __shfl_xor_sync(kFullS, Qd[e], off);
-  }
   // scale by -1 / (kT Z) and turn to charge coordinates, n_s = n*_s + sg_s d_s:
   //   va_s = bt_s sa + sg_s vd_s,  Qa_ss = va_s,
   //   Qa_ss' = bt_s bt_s' sa + bt_s sg_s' vd_s' + bt_s' sg_s vd_s + sg_s sg_s' Qd_ss'
   const float alpha = active ? -1.0f / (kT * Z) : 0.f;
   float* q_s = sQa[BWD ? team : 0];
   if (lt == 0) {
-    const float sa_a = alpha * sa;
-    float va[K], vda[K], bt[K];
+    const float sa_a = alpha * qd[0];
 #pragma unroll
     for (int s = 0; s < K; ++s) {
-      bt[s] = ((bst >> s) & 1u) ? 1.f : 0.f;
-      vda[s] = alpha * vd[s];
-      va[s] = bt[s] * sa_a + sgn[s] * vda[s];
-    }
+      const float bts = ((bst >> s) & 1u) ? 1.f : 0.f;
+      const float vs = alpha * qd[1 + s];
+      const float va = bts * sa_a + sgn[s] * vs;
+      q_s[s * K - s * (s - 1) / 2] = va;
+      q_s[tri(K) + s] = va;
 #pragma unroll
-    for (int s = 0; s < K; ++s) {
-      q_s[s * K - s * (s - 1) / 2] = va[s];
-#pragma unroll
-      for (int s2 = s + 1; s2 < K; ++s2)
+      for (int s2 = s + 1; s2 < K; ++s2) {
+        const float bt2 = ((bst >> s2) & 1u) ? 1.f : 0.f;
+        const float v2 = alpha * qd[1 + s2];
         q_s[s * K - s * (s - 1) / 2 + (s2 - s)] =
-            bt[s] * bt[s2] * sa_a + bt[s] * sgn[s2] * vda[s2] + bt[s2] * sgn[s] * vda[s] +
-            sgn[s] * sgn[s2] * alpha * Qd[s * (2 * K - s - 1) / 2 + (s2 - s - 1)];
-      q_s[tri(K) + s] = va[s];
+            bts * bt2 * sa_a + bts * sgn[s2] * v2 + bt2 * sgn[s] * vs +
+            sgn[s] * sgn[s2] * alpha * qd[1 + K + s * (2 * K - s - 1) / 2 + (s2 - s - 1)];
+      }
     }
     q_s[tri(K) + K] = sa_a;
   }

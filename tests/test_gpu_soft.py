@@ -223,3 +223,38 @@ def test_backward_with_forward_context_matches_oracle(qa, closed):
     assert np.abs(dG.cpu().numpy() - oG).max() <= GRAD_RTOL * sc
     np.testing.assert_allclose(dC.cpu().numpy(), dC2.cpu().numpy(), atol=1e-5 * sc)
     np.testing.assert_allclose(dG.cpu().numpy(), dG2.cpu().numpy(), atol=1e-5 * sc)
+
+
+def test_backward_context_after_other_calls_on_the_model(qa):
+    # the backward with the forward's context reuses that forward's prep
+    # records only while they are in place: a ground-state call or a soft
+    # call on another raster in between replaces them, and the backward must
+    # still give the oracle gradient
+    import torch
+    cfg = inputs.grid8(W=29, H=21, kT=0.02)
+    kT = 0.02
+    ras = cfg["raster"]
+    other = dict(ras, W=17, H=13, x0=ras["x0"] + 0.3)
+    P, n = 29 * 21, 8
+    gbar = np.random.Generator(np.random.PCG64(9)).normal(size=(P, n))
+    _, oC, oG = oracle.soft_grad(cfg["Cdd"], cfg["Cgd"], gbar, raster=ras, kT=kT)
+    sc = max(np.abs(oC).max(), np.abs(oG).max())
+    m = qa.Model(cfg["Cdd"], cfg["Cgd"])
+    g = torch.tensor(gbar, dtype=torch.float32, device="cuda").contiguous()
+    for between in ("ground_state", "soft_other_raster", "model_update"):
+        mean = torch.empty((P, n), dtype=torch.float32, device="cuda")
+        pctx = torch.empty(P, dtype=torch.int64, device="cuda")
+        qa.qa_soft_occupation_ctx(m.handle, ras, kT, 1.0, False, 0, mean, None, pctx)
+        if between == "ground_state":
+            m.ground_state_open(other)
+        elif between == "soft_other_raster":
+            m.soft_occupation(other, kT)
+        else:
+            qa.qa_model_update(m.handle, cfg["Cdd"], cfg["Cgd"])
+        dC = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        dG = torch.empty((n, m.n_gate), dtype=torch.float64, device="cuda")
+        qa.qa_soft_occupation_backward_ctx(m.handle, ras, kT, 1.0, False, 0, g, mean, pctx, dC, dG)
+        torch.cuda.synchronize()
+        assert np.abs(dC.cpu().numpy() - oC).max() <= GRAD_RTOL * sc, between
+        assert np.abs(dG.cpu().numpy() - oG).max() <= GRAD_RTOL * sc, between
+    m.close()
