@@ -349,6 +349,8 @@ struct SearchShared {
   int sdot[kSearchThreads][kMaxDot];
   float sh[kSearchThreads][kMaxDot];
   __align__(16) float colt[kSearchThreads / kTeamFinishMin][4 * kColStride];
+  __align__(16) float itab[kSearchThreads / kTeamFinishMin][(1 << kItMax) * kItStride];
+  __align__(16) float cslot[kSearchThreads][kItMax];
   unsigned long long red64[kSearchThreads / 32];
   unsigned red32[kSearchThreads / 32];
 };
@@ -399,12 +401,16 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
   float* colt = TF ? sh.colt[team] : nullptr;
   if (TF) {
     static_assert(L2 <= 4 && L1 + L2 <= kColStride, "column table layout");
-    if (active) col_build<L1, L2>(sM, sv, lt, T, colt);
+    if (active) {
+      col_build<L1, L2>(sM, sv, lt, T, colt);
+      if (L1 + L2 >= 9) iter_build<L1, L2>(sM, sv, lt, T, sh.itab[team]);
+    }
     __syncwarp();
   }
   if (active)
     search_lane<L1, L2, CLOSED, false, TF>(sM, sv, lt, T, 0.f, nullptr, nullptr, 0u, m1, b1,
-                                           m2, ev, colt);
+                                           m2, ev, colt, TF ? sh.itab[team] : nullptr,
+                                           sh.cslot[threadIdx.x]);
   // best (block or candidate) with its id, and the second-best minimum
   for (int off = 1; off < T; off <<= 1) {
     const float om1 = __shfl_xor_sync(kFull, m1, off);

@@ -108,6 +108,8 @@ __device__ __forceinline__ float inner_min_closed(float A, const float* q,
 // middle slot m, kColStride floats holding M(inner j, m) at j < L1 and
 // M(middle m', m) at L1 + m' (0 on the diagonal and for absent slots).
 constexpr int kColStride = 12;  // >= L1 + L2 for every split, a multiple of 4
+constexpr int kItMax = 4;       // iteration bits of a block-level search with L1 + L2 >= 9
+constexpr int kItStride = 12;   // >= 1 + L1 + L2, a multiple of 4
 
 // Per-pixel slot data staged by the team: dot of each slot, h of each slot.
 struct SlotView {
@@ -156,8 +158,14 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
                                             unsigned* bcount, unsigned bcap,
                                             float& m1, unsigned& b1, float& m2,
                                             unsigned long long& evaluated,
-                                            const float* __restrict__ colt = nullptr) {
+                                            const float* __restrict__ colt = nullptr,
+                                            const float* __restrict__ itab = nullptr,
+                                            float* __restrict__ cslot = nullptr) {
   static_assert(L1 >= 2 && L1 <= 6 && L2 >= 0 && L2 <= 5, "search split");
+  // block-level searches with at least 9 inner + middle slots take the
+  // iteration slots' terms from the team table itab (iter_build): at most 7
+  // outer slots, at least 3 of them lane bits, so at most kItMax iteration bits
+  constexpr bool ITAB = BLOCKS && (L1 + L2 >= 9);
   constexpr int NI = 1 << L1;
   constexpr int NM = 1 << L2;
   const int k = sv.k;
@@ -265,6 +273,20 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
         for (int m = 0; m < L2; ++m) gt[m] = fmaf(wO[i], Mrow[dM[m]], gt[m]);
       }
     }
+    if (ITAB) {
+      // the lane's pair terms with each iteration slot (its own lane slots
+      // present), kept in the lane's slot of shared memory
+#pragma unroll
+      for (int ii = 0; ii < kItMax; ++ii) {
+        float c = 0.f;
+        if (ii < nit) {
+          const float* Mrow = sM + sv.dot[L1 + L2 + nlb + ii] * kLdM;
+#pragma unroll
+          for (int i = 0; i < kLaneBits; ++i) c = fmaf(wO[i], Mrow[dO[i]], c);
+        }
+        cslot[ii] = c;
+      }
+    }
   }
 
   for (unsigned it = 0; it < niter; ++it) {
@@ -276,6 +298,22 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
     for (int j = 0; j < L1; ++j) q[j] = qt[j];
 #pragma unroll
     for (int m = 0; m < L2; ++m) gm[m] = gt[m];
+    if (ITAB) {
+      // A = At + the lane's pair terms with the set iteration slots + the
+      // team's terms of those slots among themselves; q, gm from the table
+      const float4 cc = *reinterpret_cast<const float4*>(cslot);
+      const float* row = itab + it * kItStride;
+      float x = 0.f;
+      x = fmaf((it & 1u) ? 1.f : 0.f, cc.x, x);
+      x = fmaf((it & 2u) ? 1.f : 0.f, cc.y, x);
+      x = fmaf((it & 4u) ? 1.f : 0.f, cc.z, x);
+      x = fmaf((it & 8u) ? 1.f : 0.f, cc.w, x);
+      A = (A + x) + row[0];
+#pragma unroll
+      for (int j = 0; j < L1; ++j) q[j] += row[1 + j];
+#pragma unroll
+      for (int m = 0; m < L2; ++m) gm[m] += row[1 + L1 + m];
+    } else
     // the iteration-bit slots (the same for the whole team), each paired
     // with the lane slots and with the iteration slots below it
     for (unsigned ib = it; ib; ib &= ib - 1u) {
@@ -387,6 +425,43 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
   m1 = best;
   b1 = Sbits | bb;
   m2 = fminf(g2, second);
+}
+
+// Team table of the iteration slots (the outer slots above a team's lane
+// bits, the same for every lane): for each iteration pattern it, kItStride
+// floats holding the sum over its set slots s of h_s + M_ss / 2 plus the
+// pairs among them (at 0), of M(inner j, s) (at 1 + j) and of M(middle m, s)
+// (at 1 + L1 + m).  Team-cooperative (lane lt of T); sync after.
+template <int L1, int L2>
+__device__ __forceinline__ void iter_build(const float* sM, const SlotView& sv, int lt, int T,
+                                           float* itab) {
+  const int k = sv.k;
+  const int nmid = min(max(k - L1, 0), L2);
+  const int nout = max(k - L1 - L2, 0);
+  const int nlb = min(__ffs(T) - 1, nout);
+  const int nit = nout - nlb;
+  const int s0 = L1 + L2 + nlb;  // the first iteration slot
+  for (int e = lt; e < (1 << nit) * kItStride; e += T) {
+    const unsigned it = (unsigned)(e / kItStride);
+    const int v = e % kItStride;
+    float acc = 0.f;
+    for (unsigned ib = it; ib; ib &= ib - 1u) {
+      const int ii = __ffs(ib) - 1;
+      const int d = sv.dot[s0 + ii];
+      const float* Mrow = sM + d * kLdM;
+      if (v == 0) {
+        float add = sv.h[s0 + ii] + 0.5f * Mrow[d];
+        for (unsigned prev = it & ((1u << ii) - 1u); prev; prev &= prev - 1u)
+          add += Mrow[sv.dot[s0 + __ffs(prev) - 1]];
+        acc += add;
+      } else if (v <= L1) {
+        if (v - 1 < k) acc += Mrow[sv.dot[v - 1]];
+      } else if (v <= L1 + L2) {
+        if (v - 1 - L1 < nmid) acc += Mrow[sv.dot[v - 1]];
+      }
+    }
+    itab[e] = acc;
+  }
 }
 
 // Team-cooperative build of the column table (lane lt of T); sync after.
