@@ -1246,14 +1246,33 @@ int qa_batch_create(const qa_batch_item* items, int count, qa_batch** out) {
       scost.push_back(c * (double)cnt);
     }
   }
+  // group the search units by kernel variant (4 klass + 2 closed + team
+  // finish), largest first within a group; one persistent grid per variant
+  auto variant = [&](const qa::WorkUnit& w) {
+    const qa::ArrayDesc& d = table[(size_t)w.array];
+    return 4 * d.klass + 2 * (d.mt.closed ? 1 : 0) + (d.cfg.T >= qa::kTeamFinishMin ? 1 : 0);
+  };
   std::vector<size_t> order(su.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](size_t x, size_t y) { return scost[x] > scost[y]; });
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+    const int vx = variant(su[x]), vy = variant(su[y]);
+    return vx != vy ? vx < vy : scost[x] > scost[y];
+  });
   std::vector<qa::WorkUnit> su_sorted(su.size());
   for (size_t i = 0; i < order.size(); ++i) su_sorted[i] = su[order[i]];
-
-  const int grid_prep = b->num_sms * pps, grid_search = b->num_sms * sps;
+  int var_first[16] = {}, var_count[16] = {}, var_grid[16] = {}, var_bc[16] = {};
+  for (size_t i = 0; i < su_sorted.size(); ++i) {
+    const int v = variant(su_sorted[i]);
+    if (var_count[v]++ == 0) var_first[v] = (int)i;
+  }
+  int grid_search = 0;
+  for (int v = 0; v < 16; ++v) {
+    if (!var_count[v]) continue;
+    var_bc[v] = grid_search;
+    var_grid[v] = std::min(var_count[v], b->num_sms * qa::batch_search_occupancy(v));
+    grid_search += var_grid[v];
+  }
+  const int grid_prep = b->num_sms * pps;
   const size_t Ptot = (size_t)std::max(1LL, b->pixels);
   const size_t off_cnt = 0;
   const size_t off_tab = align_up(sizeof(qa::Counters), 256);
@@ -1302,6 +1321,12 @@ int qa_batch_create(const qa_batch_item* items, int count, qa_batch** out) {
   L.bc_search = (qa::BlockCounts*)(mem + off_bcs);
   L.grid_prep = grid_prep;
   L.grid_search = grid_search;
+  for (int v = 0; v < 16; ++v) {
+    L.var_first[v] = var_first[v];
+    L.var_count[v] = var_count[v];
+    L.var_grid[v] = var_grid[v];
+    L.var_bc[v] = var_bc[v];
+  }
   L.num_sms = b->num_sms;
   L.ev = nullptr;
   *out = b;

@@ -1,10 +1,11 @@
 // qa_batch.cu -- the batched ground state: many arrays (any N, raster size,
 // open or closed) in one persistent prep launch and one persistent search
-// launch.  Blocks take work units -- a run of pixels of one array -- from a
-// device queue (an atomic counter over a unit table ordered largest first),
-// stage that array's constants when it changes, and run the same tile code as
-// the single-array kernels.  The near-tie and FP64 lists are then settled by
-// the list kernels shared with the single-array path.
+// launch per kernel variant present (split, form, team finish).  Blocks take
+// work units -- a run of pixels of one array -- from a device queue (an
+// atomic counter over a unit table ordered largest first), stage that array's
+// constants when it changes, and run the same tile code as the single-array
+// kernels.  The near-tie and FP64 lists are then settled by the list kernels
+// shared with the single-array path.
 #include "qa_gs_tiles.cuh"
 
 namespace qa {
@@ -43,32 +44,23 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_batch(GsLaunch L) {
   }
 }
 
-template <int L1, int L2>
-__device__ __forceinline__ void search_any(const GsLaunch& L, const ArrayDesc& a,
-                                           SearchShared& sh, int array, long long tb,
-                                           long long end, SearchAcc& acc) {
-  const bool tf = a.cfg.T >= kTeamFinishMin;
-  if (a.mt.closed) {
-    if (tf) search_tile<L1, L2, true, true>(L, a, sh, array, tb, end, acc);
-    else search_tile<L1, L2, true, false>(L, a, sh, array, tb, end, acc);
-  } else {
-    if (tf) search_tile<L1, L2, false, true>(L, a, sh, array, tb, end, acc);
-    else search_tile<L1, L2, false, false>(L, a, sh, array, tb, end, acc);
-  }
-}
-
-__global__ void __launch_bounds__(kSearchThreads) k_search_batch(GsLaunch L) {
+// The search of one kernel variant (split, form, team finish): a persistent
+// grid over that variant's units, so that every variant runs with its own
+// register count (one kernel over all of them needs the largest).
+template <int L1, int L2, bool CLOSED, bool TF>
+__global__ void __launch_bounds__(kSearchThreads) k_search_batch(GsLaunch L, int v) {
   __shared__ SearchShared sh;
   __shared__ int s_unit;
   int staged = -1;
   SearchAcc acc;
+  const int first = L.var_first[v], count = L.var_count[v];
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_unit = (int)atomicAdd(&L.cnt->q_search, 1u);
+    if (threadIdx.x == 0) s_unit = (int)atomicAdd(&L.cnt->q_var[v], 1u);
     __syncthreads();
     const int u = s_unit;
-    if (u >= L.n_search_units) break;
-    const WorkUnit wu = L.search_units[u];
+    if (u >= count) break;
+    const WorkUnit wu = L.search_units[first + u];
     const ArrayDesc& a = L.table[wu.array];
     if (wu.array != staged) {
       stage_consts(&a.md->k, &sh.cs);
@@ -77,17 +69,11 @@ __global__ void __launch_bounds__(kSearchThreads) k_search_batch(GsLaunch L) {
     }
     const int tpb = kSearchThreads / a.cfg.T;
     const long long end = wu.first + wu.count;
-    for (long long tb = wu.first; tb < end; tb += tpb) {
-      switch (a.klass) {
-        case 0: search_any<2, 0>(L, a, sh, wu.array, tb, end, acc); break;
-        case 1: search_any<4, 0>(L, a, sh, wu.array, tb, end, acc); break;
-        case 2: search_any<4, 3>(L, a, sh, wu.array, tb, end, acc); break;
-        default: search_any<5, 4>(L, a, sh, wu.array, tb, end, acc); break;
-      }
-    }
+    for (long long tb = wu.first; tb < end; tb += tpb)
+      search_tile<L1, L2, CLOSED, TF>(L, a, sh, wu.array, tb, end, acc);
   }
   if (threadIdx.x == 0) {
-    BlockCounts& o = L.bc_search[blockIdx.x];
+    BlockCounts& o = L.bc_search[L.var_bc[v] + blockIdx.x];
     o.evaluated = acc.evaluated;
     o.near_tie = acc.near_tie;
     o.boundary = acc.boundary;
@@ -95,14 +81,32 @@ __global__ void __launch_bounds__(kSearchThreads) k_search_batch(GsLaunch L) {
   }
 }
 
-// Resident blocks per SM of the two persistent kernels.
+// The kernel of variant v = 4 klass + 2 closed + team finish.
+typedef void (*BatchSearchKernel)(GsLaunch, int);
+static BatchSearchKernel batch_search_kernel(int v) {
+#define QA_V(l1, l2)                                                                   \
+  k_search_batch<l1, l2, false, false>, k_search_batch<l1, l2, false, true>,          \
+      k_search_batch<l1, l2, true, false>, k_search_batch<l1, l2, true, true>
+  static const BatchSearchKernel table[16] = {QA_V(2, 0), QA_V(4, 0), QA_V(4, 3), QA_V(5, 4)};
+#undef QA_V
+  return (v >= 0 && v < 16) ? table[v] : nullptr;
+}
+
+int batch_search_occupancy(int v) {
+  int nb = 0;
+  const BatchSearchKernel k = batch_search_kernel(v);
+  if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kSearchThreads, 0) != cudaSuccess)
+    return 1;
+  return nb < 1 ? 1 : nb;
+}
+
+// Resident blocks per SM of the persistent prep kernel and of the search of
+// the widest variant (open, 5 + 4 split, team finish), for unit sizing.
 void batch_occupancy(int* prep_per_sm, int* search_per_sm) {
-  *prep_per_sm = *search_per_sm = 1;
+  *prep_per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(prep_per_sm, k_prep_batch, kPrepThreads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(search_per_sm, k_search_batch,
-                                                kSearchThreads, 0);
   if (*prep_per_sm < 1) *prep_per_sm = 1;
-  if (*search_per_sm < 1) *search_per_sm = 1;
+  *search_per_sm = batch_search_occupancy(4 * 3 + 1);
 }
 
 cudaError_t launch_ground_state_batch(const GsLaunch& L, cudaStream_t st) {
@@ -110,7 +114,8 @@ cudaError_t launch_ground_state_batch(const GsLaunch& L, cudaStream_t st) {
   cudaMemsetAsync(L.cnt, 0, sizeof(Counters), st);
   k_prep_batch<<<L.grid_prep, kPrepThreads, 0, st>>>(L);
   if (L.ev) cudaEventRecord(L.ev[1], st);
-  k_search_batch<<<L.grid_search, kSearchThreads, 0, st>>>(L);
+  for (int v = 0; v < 16; ++v)
+    if (L.var_count[v] > 0) batch_search_kernel(v)<<<L.var_grid[v], kSearchThreads, 0, st>>>(L, v);
   if (L.ev) cudaEventRecord(L.ev[2], st);
   launch_lists(L, st);
   if (L.ev) cudaEventRecord(L.ev[3], st);

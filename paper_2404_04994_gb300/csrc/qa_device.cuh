@@ -154,6 +154,7 @@ struct Counters {
   unsigned int n_tie;   // length of the near-tie list
   unsigned int q_prep;  // batched launch: work-queue heads
   unsigned int q_search;
+  unsigned int q_var[16];  // batched launch: the search queue of each kernel variant
 };
 
 // A pixel queued for the near-tie resolve or the FP64 recheck: its array (0

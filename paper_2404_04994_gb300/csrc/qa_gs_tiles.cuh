@@ -13,12 +13,10 @@ namespace qa {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPrepThreads = 128;
-constexpr int kSearchThreads = 128;
 constexpr int kRecheckThreads = 128;
 constexpr int kResolveThreads = 256;
 constexpr int kCheckL1 = 4, kCheckL2 = 3;  // resolve/recheck split: 2^9 outer states at k = 16
 constexpr unsigned kBcap = 1024;
-constexpr int kTeamFinishMin = 8;
 
 // One charge of the output map: int8 (saturating at 127) or int16 (at
 // 32767) by the array's output width; saturation sets kFlagOverflow.

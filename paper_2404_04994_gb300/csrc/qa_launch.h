@@ -36,6 +36,9 @@ struct ArrayDesc {
   uint8_t* out_flags;
 };
 
+constexpr int kSearchThreads = 128;  // threads of a search block
+constexpr int kTeamFinishMin = 8;    // teams at least this wide finish the winning block together
+
 // Pixels [first, first + count) of one array of a batched call.
 struct WorkUnit {
   int array;
@@ -56,6 +59,11 @@ struct GsLaunch {
   BlockCounts* bc_prep;        // scratch [prep blocks]
   BlockCounts* bc_search;      // scratch [search blocks]
   int grid_prep, grid_search;  // batched call: persistent grid sizes
+  // batched call: the search units grouped by kernel variant v = 4 klass +
+  // 2 closed + team finish (units [var_first, var_first + var_count) of
+  // search_units, largest first within a group), one persistent grid of
+  // var_grid blocks per variant, its block counts from bc_search + var_bc
+  int var_first[16], var_count[16], var_grid[16], var_bc[16];
   int num_sms;
   int prep_zeroes_counters;  // single-array call: k_prep clears *cnt (no memset)
   cudaEvent_t* ev;     // optional: events around prep / search / resolve+recheck
@@ -105,6 +113,7 @@ bool search_cfg_supported(const SearchCfg& c);
 int search_klass(const SearchCfg& c);
 // Resident blocks per SM of the persistent batched kernels.
 void batch_occupancy(int* prep_per_sm, int* search_per_sm);
+int batch_search_occupancy(int variant);  // resident blocks per SM of a variant's kernel
 
 struct SoftLaunch {
   const ModelData* md;
