@@ -228,6 +228,17 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
         if (live) x = xr;
         if (bad) flags |= kFlagBoundary;
         else bx = bx2;
+        // closed with every dot but one active: the sum constraint makes the
+        // relaxed minimum the vertex N_hat e_j exactly, so once every
+        // multiplier is certainly positive no rounding error is left in x
+        // and the floor decisions need no margin
+        if (CLOSED && !bad && __popc(Af) == n - 1) {
+          const bool zpos = lt >= n - 1 || sh.qz[tb + lt] + sh.qzl[tb + lt] > 0.25f * bx2;
+          if (tballot(!zpos) == 0u) {
+            if (live) x = ((Af >> lt) & 1u) ? df{0.f, 0.f} : df{(float)nhat, 0.f};
+            bx = 0.f;
+          }
+        }
         qp_set = Af;
       }
       __syncwarp(tmask);

@@ -4,6 +4,10 @@ Rules (the FP32 search is held to the FP64 oracle):
 * a pixel is *comparable* when the oracle's best/runner-up energy gap and its
   floor / threshold decision margins all exceed 1e-9 (and its QP, if any,
   certified); comparable pixels must match bit-exactly;
+* closed arrays: a pixel whose relaxed minimum is a vertex N_hat e_j (every
+  other dot active) is comparable whatever its floor margin: that integer
+  point is the exact minimum and lies in every candidate set a rounding of
+  x_j can give;
 * energies agree within 1e-5 * max(|U|, max_i M_ii / 2);
 * non-comparable pixels are counted and reported, never silently compared.
 """
@@ -15,17 +19,30 @@ GAP_EPS = 1e-9
 U_RTOL = 1e-5
 
 
-def comparable(rec):
-    return ((rec["U2"] - rec["U"] > GAP_EPS) & (rec["margin_floor"] > GAP_EPS)
+def vertex(rec, n):
+    """Closed-array pixels whose relaxed minimum has one nonzero, integral
+    coordinate (all other dots active at exactly 0)."""
+    x = rec["x"][:, :n]
+    pos = x > 0.0
+    one = (pos.sum(1) == 1) & ((x == 0.0) | pos).all(1)
+    xj = np.where(pos, x, 0.0).sum(1)
+    return one & (np.abs(xj - np.rint(xj)) < GAP_EPS)
+
+
+def comparable(rec, n=None, closed=False):
+    floor_ok = rec["margin_floor"] > GAP_EPS
+    if closed:
+        floor_ok = floor_ok | vertex(rec, n)
+    return ((rec["U2"] - rec["U"] > GAP_EPS) & floor_ok
             & (rec["margin_thresh"] > GAP_EPS) & (rec["qp_cert"] < 1e-9)
             & (rec["status"] == 0))
 
 
-def compare(n_gpu, U_gpu, flags, rec, Cdd, label=""):
+def compare(n_gpu, U_gpu, flags, rec, Cdd, label="", closed=False):
     """Assert parity; returns a small report dict."""
     n = Cdd.shape[0]
     M = np.linalg.inv(Cdd)
-    ok = comparable(rec)
+    ok = comparable(rec, n, closed)
     want = rec["n"][:, :n]
     got = np.asarray(n_gpu).reshape(-1, n).astype(np.int64)
     bad = ok & (got != want).any(1)

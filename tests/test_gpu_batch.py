@@ -41,7 +41,8 @@ def test_batch_matches_oracle_and_single_calls(qa):
         f = f.cpu().numpy().reshape(-1)
         rec = oracle.ground_state(sp["Cdd"], sp["Cgd"], raster=sp["raster"], t=sp["threshold"],
                                   closed=sp["closed"], n_charges=sp["n_charges"])
-        compare(n, U, f, rec, sp["Cdd"], f"batch N={nd} closed={sp['closed']}")
+        compare(n, U, f, rec, sp["Cdd"], f"batch N={nd} closed={sp['closed']}",
+                closed=sp["closed"])
         m = qa.Model(sp["Cdd"], sp["Cgd"])
         if sp["closed"]:
             n1, U1, _ = m.ground_state_closed(sp["raster"], sp["n_charges"], threshold=sp["threshold"])
@@ -121,7 +122,8 @@ def test_full_size_batch_graph_sampled_against_oracle(qa):
                                       closed=sp["closed"], n_charges=sp["n_charges"],
                                       pixels=(p0, p1))
             rep = compare(n[p0:p1], U[p0:p1], f[p0:p1], rec, sp["Cdd"],
-                          f"batch array {a} N={nd} closed={sp['closed']} row {row}")
+                          f"batch array {a} N={nd} closed={sp['closed']} row {row}",
+                          closed=sp["closed"])
             compared += rep["comparable"]
     assert compared > 0.9 * sum(3 * specs[a]["raster"]["W"] for a in chosen)
     b.close()
@@ -151,5 +153,5 @@ def test_autotuned_batch_matches_oracle_at_the_tuned_thresholds(qa):
                                   closed=sp["closed"], n_charges=sp["n_charges"])
         compare(n.cpu().numpy().reshape(-1, nd), U.cpu().numpy().reshape(-1),
                 f.cpu().numpy().reshape(-1), rec, sp["Cdd"],
-                f"tuned N={nd} t={sp['threshold']:.3f} team={sp['team']}")
+                f"tuned N={nd} t={sp['threshold']:.3f} team={sp['team']}", closed=sp["closed"])
     b.close()

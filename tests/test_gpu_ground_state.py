@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_2404_04994_gb300 import inputs
-from parity import compare
+from parity import compare, vertex
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +49,7 @@ def test_chain4_full_raster(qa, closed):
     cfg = inputs.chain4(closed=closed)
     n, U, f, st = _gpu(qa, cfg)
     rec = _oracle(cfg)
-    compare(n, U, f, rec, cfg["Cdd"], f"chain4 closed={closed}")
+    compare(n, U, f, rec, cfg["Cdd"], f"chain4 closed={closed}", closed=closed)
     if closed:
         assert (n.sum(1) == 4).all()
 
@@ -93,7 +93,7 @@ def test_grid16_full_diagram_every_pixel(qa):
 def test_closed_threshold_doubling(qa, t):
     cfg = inputs.chain4(W=33, H=29, closed=True)
     n, U, f, st = _gpu(qa, cfg, t=t)
-    compare(n, U, f, _oracle(cfg, t=t), cfg["Cdd"], f"closed t={t}")
+    compare(n, U, f, _oracle(cfg, t=t), cfg["Cdd"], f"closed t={t}", closed=True)
     assert (n.sum(1) == 4).all()
     if t == 0.0:
         assert st["doubled"] > 0
@@ -132,7 +132,27 @@ def test_other_dot_counts(qa, nd):
     for closed in (False, True):
         n, U, f, _ = _gpu(qa, cfg, closed=closed, n_charges=nd)
         compare(n, U, f, _oracle(cfg, closed=closed, n_charges=nd), Cdd,
-                f"N={nd} closed={closed}")
+                f"N={nd} closed={closed}", closed=closed)
+
+
+@pytest.mark.parametrize("nd,t", [(2, 1.0), (3, 1.0), (3, 0.5), (4, 1.0)])
+def test_closed_vertex_minima_settle_without_fp64(qa, nd, t):
+    # closed, every dot but one empty: the relaxed minimum is N_hat e_j, an
+    # integer point, so it is the ground state and needs no FP64 recheck
+    rng = inputs.rng_for(70 + nd)
+    Cdd, Cgd = inputs.random_model(rng, nd, nn=(0.05, 0.25), off=(0.0, 0.1))
+    gx, gy = inputs.swept_gates(nd)
+    V = inputs.offsets(rng, nd, (gx, gy))
+    cfg = {"Cdd": Cdd, "Cgd": Cgd, "raster": inputs.raster(nd, gx, gy, V, lo=-6.0, hi=12.0, W=41, H=37),
+           "t": t, "closed": True, "n_charges": nd}
+    n, U, f, st = _gpu(qa, cfg)
+    rec = _oracle(cfg)
+    vx = vertex(rec, nd)
+    assert vx.sum() >= 50
+    compare(n, U, f, rec, Cdd, f"closed N={nd} vertices", closed=True)
+    j = np.argmax(rec["x"][:, :nd], axis=1)
+    np.testing.assert_array_equal(n[vx], nd * np.eye(nd, dtype=np.int64)[j[vx]])
+    assert ((f[vx] & 2) != 0).mean() < 0.02
 
 
 def test_single_pixel_and_negative_carrier(qa):
@@ -146,7 +166,7 @@ def test_closed_zero_charges(qa):
     cfg = inputs.chain4(W=9, H=7, closed=True)
     n, U, f, _ = _gpu(qa, cfg, n_charges=0)
     assert (n == 0).all()
-    compare(n, U, f, _oracle(cfg, n_charges=0), cfg["Cdd"], "N_hat = 0")
+    compare(n, U, f, _oracle(cfg, n_charges=0), cfg["Cdd"], "N_hat = 0", closed=True)
 
 
 def test_points_match_raster(qa):
