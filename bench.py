@@ -252,7 +252,8 @@ def run_ours(args):
     peak = n_sm * 128 * sm_max * 1e6 / 1e12   # FP32 lanes x clock
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
                 "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": search_traffic(),
-                "kernel": "k_search<5,4,open>", "ops_per_launch": ops,
+                "kernel": "k_ground_state<5,4,open> (prep + search of each tile)",
+                "ops_per_launch": ops,
                 "ops_per_evaluated_slot": ops_per_slot,
                 "search_ms": round(ms_s, 5), "prep_ms": round(statistics.mean(prep_ms), 5),
                 "recheck_ms": round(statistics.mean(recheck_ms), 5),
@@ -322,8 +323,8 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": world * P / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)},
-            # per step: k_prep, k_search, k_resolve, k_recheck
-            "gpu_launches": 4 * args.steps, "clocks": clk, "extra": extra}
+            # per step: k_ground_state (prep + search), k_resolve, k_recheck
+            "gpu_launches": 3 * args.steps, "clocks": clk, "extra": extra}
     if rank == 0:
         print(json.dumps(line))
     m.close()

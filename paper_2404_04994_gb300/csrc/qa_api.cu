@@ -150,6 +150,9 @@ void fill_consts(int n, qa::ModelData* md) {
     k.sv2[i] = split(r);
     k.vs[i] = split(md->vs[i]);
     tot += r;
+    float al = 0.5f * k.Mhi[i * qa::kLdM + i];
+    for (int j = 0; j < i; ++j) al += std::fabs(k.Mhi[i * qa::kLdM + j]);
+    k.absl[i] = al;
   }
   k.s_s = (float)tot;
   // decision margin of an FP32 QP minimum: 8 cond(Cdd) (n + 1) u32 per unit
@@ -289,6 +292,11 @@ int ensure_workspace(qa_model* m, size_t bytes) {
   e = cudaMalloc(&m->ws, want);
   if (e != cudaSuccess) return fail(QA_ERR_NOMEM, "workspace of %zu bytes: %s", want, cudaGetErrorString(e));
   m->ws_bytes = want;
+  // the counters open the workspace; a ground-state call expects its list
+  // heads at zero
+  e = cudaMemset(m->ws, 0, sizeof(qa::Counters));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "workspace counters");
   return QA_OK;
 }
 
@@ -514,7 +522,7 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
   m->last_P = P;
   a.ev = m->timing ? m->ev : nullptr;
   m->last_kind = 1;
-  m->n_bc_prep = qa::prep_blocks(a);
+  m->n_bc_prep = qa::fused_tiles(a) ? qa::search_blocks(a) : qa::prep_blocks(a);
   m->n_bc_search = qa::search_blocks(a);
   e = qa::launch_ground_state(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "ground-state launch");

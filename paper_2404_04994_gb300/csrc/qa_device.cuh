@@ -12,6 +12,7 @@
 // fall inside the bound are re-evaluated in FP64 by the recheck kernel.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -106,6 +107,7 @@ struct __align__(16) ModelConsts {
   int pad;
   float CddLo[kMaxDot * kLdM]; // Cdd - hi part (Cdd as double-float with Cdd above)
   df sv2[kMaxDot];             // Cdd 1 as double-float
+  float absl[kMaxDot];         // M_ii / 2 + sum_{j < i} |M_ij| (FP32 hi parts, j increasing)
   float bx_qp_scale2;          // ... after one double-float refinement of the QP
   int pad2[3];
 };
@@ -155,7 +157,21 @@ struct Counters {
   unsigned int q_prep;  // batched launch: work-queue heads
   unsigned int q_search;
   unsigned int q_var[16];  // batched launch: the search queue of each kernel variant
+  unsigned int lists_done; // blocks of the FP64 recheck kernel that have finished
 };
+
+// A single-array call's first kernel clears every counter but the two list
+// heads, which its own blocks append to while others are still starting; the
+// last block of the call's FP64 recheck kernel clears those (and lists_done)
+// instead, so the heads are zero whenever a call starts.
+__device__ __forceinline__ void zero_accumulators(Counters* c) {
+  constexpr int nw = (int)(sizeof(Counters) / sizeof(unsigned));
+  constexpr int k0 = (int)(offsetof(Counters, n_flag) / sizeof(unsigned));
+  constexpr int k1 = (int)(offsetof(Counters, n_tie) / sizeof(unsigned));
+  constexpr int k2 = (int)(offsetof(Counters, lists_done) / sizeof(unsigned));
+  for (int e = threadIdx.x; e < nw; e += blockDim.x)
+    if (e != k0 && e != k1 && e != k2) reinterpret_cast<unsigned*>(c)[e] = 0u;
+}
 
 // A pixel queued for the near-tie resolve or the FP64 recheck: its array (0
 // for a single-array call), its index and the FP32 minimum of its search.

@@ -179,7 +179,15 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
   df c = {0.f, 0.f};
   if (live) {
     if (a.sc.kind == 0) {
-      const int ix = (int)(p % a.sc.W), iy = (int)(p / a.sc.W);
+      int ix, iy;
+      if (a.sc.P <= 0xffffffffLL) {  // 32-bit division when the raster allows it
+        const unsigned pu = (unsigned)p, W = (unsigned)a.sc.W;
+        iy = (int)(pu / W);
+        ix = (int)(pu - (unsigned)iy * W);
+      } else {
+        ix = (int)(p % a.sc.W);
+        iy = (int)(p / a.sc.W);
+      }
       c = raster_c(sh.sc0[lt], sh.sdu[lt], sh.sdw[lt], ix, iy);
     } else {
       c = point_c(&a.md->Cgd[lt * a.ng], &a.sc.V[p * a.ng], a.ng, a.mt.carrier);
@@ -197,9 +205,9 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
   unsigned flags = 0u;
   unsigned qp_set = 0u;
   float bx = a.bx_analytic;
-  const float cmax = tmax_f(live ? fabsf(c.hi + c.lo) : 0.f);
   if (A) {  // (a3) QP, solved by the team's first lane
     flags |= kFlagQP;
+    const float cmax = tmax_f(live ? fabsf(c.hi + c.lo) : 0.f);
     if (CLOSED && nhat == 0) {
       x = {0.f, 0.f};
     } else {
@@ -266,8 +274,8 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
     }
     if (tballot(bnd)) flags |= kFlagBoundary;
     mask = tballot(live && amb);
-    const int sum = tsum_i(live ? base : 0);
     if (!CLOSED) break;
+    const int sum = tsum_i(live ? base : 0);
     w = nhat - sum;
     if (w >= 0 && w <= __popc(mask)) break;
     if (tt >= 1.0) {  // impossible in exact arithmetic: settle in FP64
@@ -283,35 +291,55 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
   // h_i = (M (base - c))_i, r = base - c in double-float staged in the
   // team's rows of qx / qz (free after the QP); the products' high parts are
   // summed error-free and their low parts and rounding errors in plain FP32
-  // (error O(u^2) of sum |M_ij r_j|, far below the final rounding of h to FP32)
+  // (error O(u^2) of sum |M_ij r_j|, far below the final rounding of h to
+  // FP32).  Four columns per step with their loads issued together and two
+  // independent sums (even and odd columns), joined error-free at the end.
   const df r = df_sub({(float)base, 0.f}, c);
   const int tb0 = threadIdx.x - lt;
   __syncwarp(tmask);
   sh.qx[threadIdx.x] = r.hi;
   sh.qz[threadIdx.x] = r.lo;
   __syncwarp(tmask);
+  const float* Mrow = sMhi + lt * kLdM;
+  const float* Mrowl = sMlo + lt * kLdM;
   float h = 0.f;
   if (live) {
-    float shi = 0.f, slo = 0.f;
-    for (int j = 0; j < n; ++j) {
-      const float mh = sMhi[lt * kLdM + j], ml = sMlo[lt * kLdM + j];
-      const float xh = sh.qx[tb0 + j], xl = sh.qz[tb0 + j];
-      const df pr = two_prod(mh, xh);
-      const float small = __fmaf_rn(mh, xl, __fmaf_rn(ml, xh, pr.lo));
-      const df sm = two_sum(shi, pr.hi);
-      shi = sm.hi;
-      slo = __fadd_rn(slo, __fadd_rn(sm.lo, small));
+    float shi[2] = {0.f, 0.f}, slo[2] = {0.f, 0.f};
+    for (int j0 = 0; j0 < n; j0 += 4) {
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int j = j0 + jj;
+        const bool on = j < n;
+        const int jc = on ? j : 0;
+        const float mh = on ? Mrow[jc] : 0.f, ml = on ? Mrowl[jc] : 0.f;
+        const float xh = sh.qx[tb0 + jc], xl = sh.qz[tb0 + jc];
+        const df pr = two_prod(mh, xh);
+        const float small = __fmaf_rn(mh, xl, __fmaf_rn(ml, xh, pr.lo));
+        const df sm = two_sum(shi[jj & 1], pr.hi);
+        shi[jj & 1] = sm.hi;
+        slo[jj & 1] = __fadd_rn(slo[jj & 1], __fadd_rn(sm.lo, small));
+      }
     }
-    h = shi + slo;
+    const df st = two_sum(shi[0], shi[1]);
+    h = st.hi + (st.lo + (slo[0] + slo[1]));
   }
-  // S_i = |h_i| + M_ii / 2 + sum over the ambiguous j < i of |M_ij| (fixed
-  // range, no divergent loop)
+  // S_i = |h_i| + M_ii / 2 + sum over the ambiguous j < i of |M_ij|: the
+  // row's precomputed prefix when every j < i is ambiguous, else four columns
+  // per step with two independent sums
   float Si = 0.f;
-  if (live && amb) {
-    Si = fabsf(h) + 0.5f * sMhi[lt * kLdM + lt];
-    const unsigned below = mask & ((1u << lt) - 1u);
-    for (int j = 0; j < n; ++j)
-      Si += ((below >> j) & 1u) ? fabsf(sMhi[lt * kLdM + j]) : 0.f;
+  const unsigned below = mask & ((1u << lt) - 1u);
+  if (live && amb && below == (1u << lt) - 1u) {
+    Si = fabsf(h) + sh.cs.absl[lt];
+  } else if (live && amb) {
+    float sp[2] = {fabsf(h) + 0.5f * Mrow[lt], 0.f};
+    for (int j0 = 0; j0 < n; j0 += 4) {
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int j = j0 + jj;
+        sp[jj & 1] += ((below >> j) & 1u) ? fabsf(Mrow[j < n ? j : 0]) : 0.f;
+      }
+    }
+    Si = sp[0] + sp[1];
   }
   const float S = tsum_f(Si);
   const int k = __popc(mask);
@@ -368,6 +396,16 @@ struct SearchAcc {
   unsigned long long evaluated = 0;
   unsigned near_tie = 0, boundary = 0, overflow = 0;
 };
+
+// A block that prepares and then searches its own tile holds the two stages'
+// scratch in one place; the model constants, first in both, are staged once.
+union GsShared {
+  PrepShared p;
+  SearchShared s;
+};
+static_assert(offsetof(PrepShared, cs) == 0 && offsetof(SearchShared, cs) == 0,
+              "the model constants open both stages' shared state");
+static_assert(kPrepThreads == kSearchThreads, "one block size for both stages");
 
 // ---------------------------------------------------------------------------
 // (a5)-(a6), (a8) for one tile: candidate search, top-two selection, outputs.
@@ -548,6 +586,8 @@ struct ResolveShared {
   float sh[kMaxDot];
   df shd[kMaxDot];
   df sui[kMaxDot];
+  float pk[kMaxDot][kMaxDot + 1];   // pair terms of the pixel's slots, M_{dot(s) dot(s2)}
+  float pkl[kMaxDot][kMaxDot + 1];  // ... and their low parts
   unsigned blist[128];
   unsigned bcnt;
   df rbest[kResolveThreads / 32], rsec[kResolveThreads / 32];
@@ -555,11 +595,12 @@ struct ResolveShared {
   unsigned dbits;   // the decision of warp 0, for the whole block
   int dok;
   unsigned dflags;
+  df ub;            // U(base)
 };
 
 template <bool CLOSED>
 __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, ResolveShared& S,
-                                     ListEntry te, unsigned& my_res) {
+                                     ListEntry te, unsigned& my_res, unsigned& my_slmax) {
   constexpr int L1 = kCheckL1, L2 = kCheckL2;
   constexpr int NI = 1 << L1;
   constexpr int NM = 1 << L2;
@@ -583,11 +624,13 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
   const unsigned mask = rec->mask;
   const int k = __popc(mask);
   const int w = rec->w;
+  // the pixel's flags, read while the walk runs
+  const unsigned char flags0 = (tid == 0 && a.out_flags) ? a.out_flags[p] : 0;
   // h_i = (M (base - c))_i in double-float, and U(base) = r0 . h / 2: one
-  // product M_ij r_j per thread (row i = tid / 16), summed over the row's 16
-  // threads
+  // product M_ij r_j per thread of the first 256 (row i = tid / 16), summed
+  // over the row's 16 threads
   {
-    static_assert(kResolveThreads == kMaxDot * kMaxDot, "one thread per matrix entry");
+    static_assert(kResolveThreads >= kMaxDot * kMaxDot, "one thread per matrix entry");
     const int i = tid >> 4, j = tid & 15;
     df prod = {0.f, 0.f};
     if (i < n && j < n) {
@@ -614,12 +657,35 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
   }
   if (tid == 0) bcnt = 0u;
   __syncthreads();
+  // U(base) = sum_i r0_i h_i / 2, a 16-lane double-float sum in warp 0
+  if (wid == 0) {
+    df u = (lane < n) ? sui[lane] : df{0.f, 0.f};
+    for (int off = 8; off > 0; off >>= 1) {
+      df o;
+      o.hi = __shfl_xor_sync(kFull, u.hi, off, 16);
+      o.lo = __shfl_xor_sync(kFull, u.lo, off, 16);
+      u = df_add(u, o);
+    }
+    if (lane == 0) S.ub = df_mul_f(u, 0.5f);
+  }
+  // the slots' pair terms, one per thread (zero outside the k slots), for
+  // the shortlist's sums
+  {
+    const int s1 = tid >> 4, s2 = tid & 15;
+    if (s1 < kMaxDot) {
+      const bool on = s1 < k && s2 < k;
+      const int e = on ? sdot[s1] * kLdM + sdot[s2] : 0;
+      S.pk[s1][s2] = on ? sM[e] : 0.f;
+      S.pkl[s1][s2] = on ? sMlo[e] : 0.f;
+    }
+  }
   // every block whose FP32 minimum is within the bound of the search's
   const SlotView sv{sdot, sh, k, w};
   const float thr = te.m1 + rec->bound;
   float d1, d2;
   unsigned db;
   unsigned long long ev = 0;
+  static_assert(kResolveThreads <= 256, "the walk's team is the block: at most 8 lane bits");
   search_lane<L1, L2, CLOSED, true>(sM, sv, tid, kResolveThreads, thr, blist, &bcnt,
                                     kCap, d1, db, d2, ev);
   __syncthreads();
@@ -649,18 +715,16 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
       }
       df E = {0.f, 0.f};
       if (ok && ((bits >> sub) & 1u)) {
-        const int d = sdot[sub];
-        const float* Mr = sM + d * kLdM;
-        const float* Ml = sMlo + d * kLdM;
+        const float* Pr = S.pk[sub];
+        const float* Pl = S.pkl[sub];
         const unsigned below = bits & ((1u << sub) - 1u);
         float hi = shd[sub].hi, lo = shd[sub].lo;
 #pragma unroll
         for (int s2 = 0; s2 < kMaxDot - 1; ++s2) {
           const bool on = (below >> s2) & 1u;
-          const int d2 = on ? sdot[s2] : d;
-          const df t = two_sum(hi, on ? Mr[d2] : 0.f);
+          const df t = two_sum(hi, on ? Pr[s2] : 0.f);
           hi = t.hi;
-          lo = __fadd_rn(lo, __fadd_rn(t.lo, on ? Ml[d2] : 0.f));
+          lo = __fadd_rn(lo, __fadd_rn(t.lo, on ? Pl[s2] : 0.f));
         }
         E = two_sum(hi, lo);
       }
@@ -696,16 +760,26 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
   }
   if (lane == 0) { rbest[wid] = best; rsec[wid] = second; rbits[wid] = bbits; }
   __syncthreads();
-  // thread 0: merge the warps' results in warp order, U(base) = sum_i
-  // r0_i h_i / 2 in dot order, decide
+  // warp 0 merges the warps' results as a shuffle tree (the order by energy,
+  // then by the reversed bits, is total, so any merge order gives the same
+  // best and second); lane 0 decides
+  static_assert((NW & (NW - 1)) == 0 && NW <= 32, "warps of the block: a power of two");
+  if (wid == 0) {
+    const bool have = lane < NW;
+    best = have ? rbest[lane] : df{kInf, 0.f};
+    second = have ? rsec[lane] : df{kInf, 0.f};
+    bbits = have ? rbits[lane] : 0xffffffffu;
+    for (int off = NW / 2; off > 0; off >>= 1) {
+      df ob, os;
+      ob.hi = __shfl_xor_sync(kFull, best.hi, off);
+      ob.lo = __shfl_xor_sync(kFull, best.lo, off);
+      os.hi = __shfl_xor_sync(kFull, second.hi, off);
+      os.lo = __shfl_xor_sync(kFull, second.lo, off);
+      merge(ob, os, __shfl_xor_sync(kFull, bbits, off));
+    }
+  }
   if (tid == 0) {
-    best = rbest[0];
-    second = rsec[0];
-    bbits = rbits[0];
-    for (int w2 = 1; w2 < NW; ++w2) merge(rbest[w2], rsec[w2], rbits[w2]);
-    df ub = {0.f, 0.f};
-    for (int i = 0; i < n; ++i) ub = df_add(ub, sui[i]);
-    ub = df_mul_f(ub, 0.5f);
+    const df ub = S.ub;
     // exact-tie test in double-float: second - best against
     // 1e-10 (1 + |U(base)|) (no FP64 instructions on this path)
     const float gap = second.hi < kInf ? df_add(second, df_neg(best)).hi : kInf;
@@ -720,7 +794,9 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
     } else if (a.out_U) {
       a.out_U[p] = df_to_double(df_add(ub, best));
     }
-    atomicMax(&L.cnt->shortlist_max, (unsigned long long)nb);
+    // the shortlist length goes to the counters once per block, at the end
+    // of the kernel (an atomic here would hold up the barrier below)
+    my_slmax = nb > my_slmax ? nb : my_slmax;
   }
   __syncthreads();
   // the charges, one dot per thread
@@ -734,7 +810,7 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
     }
     __syncthreads();
     if (tid == 0) {
-      if (a.out_flags) a.out_flags[p] = (uint8_t)(a.out_flags[p] | kFlagRechecked | S.dflags);
+      if (a.out_flags) a.out_flags[p] = (uint8_t)(flags0 | kFlagRechecked | S.dflags);
       my_res += 1;
     }
   }

@@ -1,20 +1,22 @@
 // qa_kernels_gs.cu -- ground-state kernels for one array: one tile per block
-// for prep and search, grid-stride over the lists for resolve and recheck.
+// for prep and search (one kernel or two), grid-stride over the lists for
+// resolve and recheck.
 // The stages themselves live in qa_gs_tiles.cuh (shared with the batch).
 #include "qa_gs_tiles.cuh"
 
 namespace qa {
 
+// Prep alone: the soft path's candidate-set records, and the first stage of a
+// ground-state call whose tiling keeps prep and search apart (it clears the
+// accumulating counters; the list heads are zero on entry).
 template <bool CLOSED>
 __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch L) {
   __shared__ PrepShared sh;
   const ArrayDesc& a = L.one;
   // the search may launch now: it stages its constants and then waits for
-  // this grid's results in grid_dep_wait
+  // this grid's results
   grid_dep_signal();
-  if (L.prep_zeroes_counters && blockIdx.x == 0)
-    for (int e = threadIdx.x; e < (int)(sizeof(Counters) / sizeof(unsigned)); e += blockDim.x)
-      reinterpret_cast<unsigned*>(L.cnt)[e] = 0u;
+  if (blockIdx.x == 0) zero_accumulators(L.cnt);
   prep_stage_array(a, sh);
   PrepAcc acc;
   const long long team_base = (long long)blockIdx.x * (kPrepThreads / a.prep_team);
@@ -27,6 +29,46 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch L) {
   }
 }
 
+// Prep and search of one tile: the block prepares the pixels it then searches
+// (their records go to global memory for the list kernels and come back from
+// L1 / L2 for the search), so no grid-wide wait separates the two stages and
+// the prep of later tiles overlaps the search of earlier ones.
+template <int L1, int L2, bool CLOSED, bool TF>
+__global__ void __launch_bounds__(kSearchThreads) k_ground_state(GsLaunch L) {
+  __shared__ GsShared sh;
+  const ArrayDesc& a = L.one;
+  // the resolve may launch once every block has passed here (all are then
+  // resident or done): it stages its constants and waits for this grid
+  grid_dep_signal();
+  if (blockIdx.x == 0) zero_accumulators(L.cnt);
+  prep_stage_array(a, sh.p);
+  const long long per = kSearchThreads / a.cfg.T;
+  const long long first = (long long)blockIdx.x * per;
+  const long long last = first + per < a.sc.P ? first + per : a.sc.P;
+  PrepAcc pacc;
+  for (long long b = first; b < last; b += kPrepThreads / a.prep_team)
+    prep_tile<CLOSED>(a, sh.p, b, last, pacc);
+  if (threadIdx.x == 0) {
+    BlockCounts& o = L.bc_prep[blockIdx.x];
+    o.candidates = pacc.candidates;
+    o.qp = pacc.qp;
+    o.doubled = pacc.doubled;
+  }
+  __syncthreads();  // the tile's records are written; the prep scratch is free
+  SearchAcc acc;
+  search_tile<L1, L2, CLOSED, TF>(L, a, sh.s, 0, first, a.sc.P, acc);
+  if (threadIdx.x == 0) {
+    BlockCounts& o = L.bc_search[blockIdx.x];
+    o.evaluated = acc.evaluated;
+    o.near_tie = acc.near_tie;
+    o.boundary = acc.boundary;
+    o.overflow = acc.overflow;
+  }
+}
+
+// Search alone, behind k_prep (programmatic dependent launch): for tilings
+// where one search block covers several prep blocks' pixels, which a block
+// preparing its own tile would prepare one pass after another.
 template <int L1, int L2, bool CLOSED, bool TF>
 __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch L) {
   __shared__ SearchShared sh;
@@ -35,8 +77,7 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch L) {
   grid_dep_wait();  // the records come from k_prep
   __syncthreads();
   // every block of this grid is resident or done once all have passed here:
-  // the resolve grid may launch into the slots that free up, stage its
-  // constants and wait for this grid's results
+  // the resolve grid may launch into the slots that free up
   grid_dep_signal();
   SearchAcc acc;
   const long long team_base = (long long)blockIdx.x * (kSearchThreads / a.cfg.T);
@@ -62,7 +103,7 @@ __global__ void __launch_bounds__(kResolveThreads) k_resolve(GsLaunch L) {
   grid_dep_signal();  // the recheck may launch and stage likewise
   grid_dep_wait();    // the tie list comes from the search
   const unsigned ntie = L.cnt->n_tie;
-  unsigned my_res = 0;
+  unsigned my_res = 0, my_slmax = 0;
   for (unsigned it = blockIdx.x; it < ntie; it += gridDim.x) {
     const ListEntry te = L.tie_list[it];
     const ArrayDesc& a = desc_of(L, te.array);
@@ -73,12 +114,14 @@ __global__ void __launch_bounds__(kResolveThreads) k_resolve(GsLaunch L) {
     if (threadIdx.x == 0) S.bcnt = 0u;
     __syncthreads();
     if (a.mt.closed)
-      resolve_entry<true>(L, a, S, te, my_res);
+      resolve_entry<true>(L, a, S, te, my_res, my_slmax);
     else
-      resolve_entry<false>(L, a, S, te, my_res);
+      resolve_entry<false>(L, a, S, te, my_res, my_slmax);
     __syncthreads();
   }
   if (threadIdx.x == 0 && my_res) atomicAdd(&L.cnt->resolved, (unsigned long long)my_res);
+  if (threadIdx.x == 0 && my_slmax)
+    atomicMax(&L.cnt->shortlist_max, (unsigned long long)my_slmax);
 }
 
 // FP64 recheck list: one block per entry, grid-stride.
@@ -105,6 +148,18 @@ __global__ void __launch_bounds__(kRecheckThreads) k_recheck(GsLaunch L) {
     else
       recheck_entry<false>(L, a, S, fe);
     __syncthreads();
+  }
+  // the list heads start the next call at zero: the last block to finish
+  // clears them (every block has read n_flag by then, and the resolve, the
+  // reader of n_tie, has completed)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&L.cnt->lists_done, 1u) == gridDim.x - 1) {
+      L.cnt->n_flag = 0u;
+      L.cnt->n_tie = 0u;
+      L.cnt->lists_done = 0u;
+    }
   }
 }
 
@@ -144,27 +199,46 @@ cudaError_t launch_lists(const GsLaunch& L, cudaStream_t st) {
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+bool fused_tiles(const GsLaunch& L) {
+  // a block preparing its own tile makes (prep_team / T) prep passes over it
+  return L.one.prep_team <= 2 * L.one.cfg.T;
+}
+
 template <int L1, int L2, bool CLOSED>
-static cudaError_t run(const GsLaunch& Lin, cudaStream_t st) {
-  // k_prep clears the counters (no memset node); search, resolve and recheck
-  // start early behind their predecessor (programmatic dependent launch)
-  GsLaunch L = Lin;
-  L.prep_zeroes_counters = 1;
+static cudaError_t run(const GsLaunch& L, cudaStream_t st) {
+  // prep + search in one kernel where a search tile is at most two prep
+  // passes, else k_prep and k_search (programmatic dependent launch); the
+  // first kernel clears the accumulating counters, the list heads are zero
+  // on entry; resolve and recheck start early behind their predecessor
+  cudaError_t e = cudaSuccess;
   if (L.ev) cudaEventRecord(L.ev[0], st);
-  k_prep<CLOSED><<<prep_blocks(L), kPrepThreads, 0, st>>>(L);
-  if (L.ev) cudaEventRecord(L.ev[1], st);
-  cudaError_t e;
-  if (L.one.cfg.T >= kTeamFinishMin)
-    e = launch_dependent(k_search<L1, L2, CLOSED, true>, (unsigned)search_blocks(L),
-                         kSearchThreads, st, L);
-  else
-    e = launch_dependent(k_search<L1, L2, CLOSED, false>, (unsigned)search_blocks(L),
-                         kSearchThreads, st, L);
-  if (e != cudaSuccess) return e;
+  if (fused_tiles(L)) {
+    if (L.ev) cudaEventRecord(L.ev[1], st);
+    if (L.one.cfg.T >= kTeamFinishMin)
+      k_ground_state<L1, L2, CLOSED, true><<<search_blocks(L), kSearchThreads, 0, st>>>(L);
+    else
+      k_ground_state<L1, L2, CLOSED, false><<<search_blocks(L), kSearchThreads, 0, st>>>(L);
+    e = cudaGetLastError();
+  } else {
+    k_prep<CLOSED><<<prep_blocks(L), kPrepThreads, 0, st>>>(L);
+    e = cudaGetLastError();
+    if (L.ev) cudaEventRecord(L.ev[1], st);
+    if (e == cudaSuccess) {
+      if (L.one.cfg.T >= kTeamFinishMin)
+        e = launch_dependent(k_search<L1, L2, CLOSED, true>, (unsigned)search_blocks(L),
+                             kSearchThreads, st, L);
+      else
+        e = launch_dependent(k_search<L1, L2, CLOSED, false>, (unsigned)search_blocks(L),
+                             kSearchThreads, st, L);
+    }
+  }
   if (L.ev) cudaEventRecord(L.ev[2], st);
-  e = launch_lists(L, st);
+  if (e == cudaSuccess) e = launch_lists(L, st);
   if (L.ev) cudaEventRecord(L.ev[3], st);
-  return e != cudaSuccess ? e : cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
+  // a chain cut short leaves the list heads set: clear them for the next call
+  if (e != cudaSuccess) cudaMemsetAsync(L.cnt, 0, sizeof(Counters), st);
+  return e;
 }
 
 cudaError_t launch_prep(const GsLaunch& L, cudaStream_t st) {

@@ -55,7 +55,7 @@ struct GsLaunch {
   int n_search_units;
   ListEntry* flag_list;        // scratch: pixels for the FP64 recheck
   ListEntry* tie_list;         // scratch: near-tie pixels for the resolve kernel
-  Counters* cnt;               // scratch, zeroed at the start of each call
+  Counters* cnt;               // scratch; list heads zero at the start of each call
   BlockCounts* bc_prep;        // scratch [prep blocks]
   BlockCounts* bc_search;      // scratch [search blocks]
   int grid_prep, grid_search;  // batched call: persistent grid sizes
@@ -65,7 +65,6 @@ struct GsLaunch {
   // var_grid blocks per variant, its block counts from bc_search + var_bc
   int var_first[16], var_count[16], var_grid[16], var_bc[16];
   int num_sms;
-  int prep_zeroes_counters;  // single-array call: k_prep clears *cnt (no memset)
   cudaEvent_t* ev;     // optional: events around prep / search / resolve+recheck
 };
 
@@ -99,7 +98,9 @@ struct SensorLaunch {
 };
 cudaError_t launch_sensor(const SensorLaunch& L, cudaStream_t st);
 
-// prep -> search -> resolve -> FP64 recheck of one array, enqueued on `st`.
+// prep + search (one kernel or two) -> resolve -> FP64 recheck of one array,
+// enqueued on `st`; the counters' list heads must be zero on entry and are on
+// exit.
 cudaError_t launch_ground_state(const GsLaunch& a, cudaStream_t st);
 // The same for a batch (persistent kernels over the work queues).
 cudaError_t launch_ground_state_batch(const GsLaunch& a, cudaStream_t st);
@@ -109,6 +110,9 @@ cudaError_t launch_prep(const GsLaunch& a, cudaStream_t st);
 cudaError_t launch_lists(const GsLaunch& a, cudaStream_t st);
 int prep_blocks(const GsLaunch& a);
 int search_blocks(const GsLaunch& a);
+// true: one kernel prepares and searches each tile (block counts of both
+// stages per search block); false: k_prep then k_search
+bool fused_tiles(const GsLaunch& a);
 bool search_cfg_supported(const SearchCfg& c);
 int search_klass(const SearchCfg& c);
 // Resident blocks per SM of the persistent batched kernels.

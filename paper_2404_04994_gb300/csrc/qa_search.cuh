@@ -145,13 +145,14 @@ __device__ __forceinline__ float state_from_scratch(const float* sM,
 }
 
 // Search of one lane's share.  Lane t of a team of T (a power of two, at
-// most 256) handles the outer patterns o = t, t + T, ...; results: best energy m1 with its full slot
+// most 2^LANEBITS) handles the outer patterns o = t, t + T, ...; results: best energy m1 with its full slot
 // pattern b1, and the second-best energy m2 over the lane's candidates.
 // COLLECT: instead, append every (outer, middle) block whose minimum is
 // <= thr to blist (used by the FP64 recheck to shortlist candidates).
 // BLOCKS: return the lane's best block minimum with its block id and the
 // second-best block minimum, for a team-level finish (team_finish).
-template <int L1, int L2, bool CLOSED, bool COLLECT, bool BLOCKS = false>
+// LANEBITS: log2 of the widest team the caller uses (T <= 2^LANEBITS).
+template <int L1, int L2, bool CLOSED, bool COLLECT, bool BLOCKS = false, int LANEBITS = 8>
 __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
                                             const SlotView sv, int t, int T,
                                             float thr, unsigned* blist,
@@ -249,7 +250,7 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
   // round exactly like sums over the lane's set bits alone, but with a trip
   // count that is the same for every lane of the team: no divergent,
   // load-dependent chains.
-  constexpr int kLaneBits = 8;  // log2 of the widest team (a 256-thread block)
+  constexpr int kLaneBits = LANEBITS;
   int dO[kLaneBits];
   float wO[kLaneBits];
 #pragma unroll

@@ -123,6 +123,13 @@ __global__ void k_model_update(ModelData* md, int n, int ng, const double* Cdd,
     k.sv[tid] = __double2float_rn(r);
     k.sv2[tid] = tid < n ? df_from_double(r) : df{0.f, 0.f};
     k.vs[tid] = tid < n ? df_from_double(md->vs[tid]) : df{0.f, 0.f};
+    // the same FP32 sum as the host set-up, from the same FP32 roundings
+    float al = 0.f;
+    if (tid < n) {
+      al = 0.5f * __double2float_rn(md->M[tid * n + tid]);
+      for (int j = 0; j < tid; ++j) al += fabsf(__double2float_rn(md->M[tid * n + j]));
+    }
+    k.absl[tid] = al;
   }
   if (tid == 0) {
     double tot = 0.0;
