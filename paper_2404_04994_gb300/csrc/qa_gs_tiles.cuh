@@ -578,7 +578,9 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
 // within 1e-10 (a true tie) or whose list overflows goes on to the FP64
 // recheck, which also applies the lexicographic tie rule.  The resolve split
 // is kCheckL1 / kCheckL2 for every array; the search's bound covers it (it
-// was derived for a middle level at least as deep).
+// was derived for a middle level at least as deep).  A block runs an entry's
+// code once per launch, on cold instruction caches, so the small reductions
+// and sums below stay rolled loops: their bodies are fetched once.
 // ---------------------------------------------------------------------------
 struct ResolveShared {
   ModelConsts cs;
@@ -637,6 +639,7 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
       const df rj = df_sub({(float)rec->base[j], 0.f}, {rec->chi[j], rec->clo[j]});
       prod = df_mul({sM[i * kLdM + j], sMlo[i * kLdM + j]}, rj);
     }
+#pragma unroll 1
     for (int off = 1; off < 16; off <<= 1) {
       df o;
       o.hi = __shfl_xor_sync(kFull, prod.hi, off, 16);
@@ -660,6 +663,7 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
   // U(base) = sum_i r0_i h_i / 2, a 16-lane double-float sum in warp 0
   if (wid == 0) {
     df u = (lane < n) ? sui[lane] : df{0.f, 0.f};
+#pragma unroll 1
     for (int off = 8; off > 0; off >>= 1) {
       df o;
       o.hi = __shfl_xor_sync(kFull, u.hi, off, 16);
@@ -719,7 +723,7 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
         const float* Pl = S.pkl[sub];
         const unsigned below = bits & ((1u << sub) - 1u);
         float hi = shd[sub].hi, lo = shd[sub].lo;
-#pragma unroll
+#pragma unroll 1
         for (int s2 = 0; s2 < kMaxDot - 1; ++s2) {
           const bool on = (below >> s2) & 1u;
           const df t = two_sum(hi, on ? Pr[s2] : 0.f);
@@ -728,6 +732,7 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
         }
         E = two_sum(hi, lo);
       }
+#pragma unroll 1
       for (int off = 1; off < kSub; off <<= 1) {
         df o;
         o.hi = __shfl_xor_sync(kFull, E.hi, off, kSub);
@@ -750,6 +755,7 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
     second = less(lose, s2) ? lose : s2;
     if (take) { best = ob; bbits = obb; }
   };
+#pragma unroll 1
   for (int off = 16; off > 0; off >>= 1) {
     df ob, os;
     ob.hi = __shfl_xor_sync(kFull, best.hi, off);
@@ -769,6 +775,7 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
     best = have ? rbest[lane] : df{kInf, 0.f};
     second = have ? rsec[lane] : df{kInf, 0.f};
     bbits = have ? rbits[lane] : 0xffffffffu;
+#pragma unroll 1
     for (int off = NW / 2; off > 0; off >>= 1) {
       df ob, os;
       ob.hi = __shfl_xor_sync(kFull, best.hi, off);
