@@ -92,11 +92,12 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------
 def search_traffic():
-    """dram read+write bytes per launch of the search kernel from the committed
-    ncu summary, or None when the kernel sources changed since that capture."""
+    """dram read+write bytes per launch of the ground-state kernel (prep +
+    search) from the committed ncu summary, or None when the kernel sources
+    changed since that capture."""
     import hashlib
     import re
-    prof = os.path.join(ROOT, "profiles", "search_kernel_grid16_100x100.md")
+    prof = os.path.join(ROOT, "profiles", "ground_state_kernel_grid16_100x100.md")
     if not os.path.exists(prof):
         return None
     text = open(prof).read()
