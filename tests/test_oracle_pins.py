@@ -221,6 +221,34 @@ def test_closed_double_dot_equals_brute_force():
             np.testing.assert_array_equal(rec["n"][:2], bn)
 
 
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_closed_vertex_minimum_is_the_ground_state(n):
+    # Closed, every dot but one active in the relaxed minimum: the sum
+    # constraint puts x at the vertex N e_j, an integer point, which is then
+    # the exact integer minimum (brute force over all compositions agrees)
+    # whatever the rounding of x_j; the GPU parity rule relies on this.
+    rng = _rng(30 + n)
+    seen = 0
+    for _ in range(300):
+        Cdd, _ = inputs.random_model(rng, n, nn=(0.05, 0.3))
+        M = np.linalg.inv(Cdd)
+        c = rng.uniform(-4.0, 6.0, n)
+        N = int(rng.integers(1, 5))
+        rec = oracle.ground_state_c(Cdd, c, t=1.0, closed=True, n_charges=N)
+        x = np.asarray(rec["x"][:n])
+        if not ((x > 0).sum() == 1 and ((x == 0.0) | (x > 0)).all()):
+            continue
+        j = int(np.argmax(x))
+        assert abs(x[j] - N) < 1e-9
+        want = np.zeros(n, dtype=np.int64)
+        want[j] = N
+        np.testing.assert_array_equal(rec["n"][:n], want)
+        bn, _, _, _ = oracle.brute_force(M, c, closed=True, n_charges=N)
+        np.testing.assert_array_equal(bn, want)
+        seen += 1
+    assert seen >= 20
+
+
 def test_open_negative_region_equals_brute_force_double_dot():
     # including pixels where the analytic minimum is infeasible (QP path)
     cfg = inputs.double_dot(W=40, H=40)
