@@ -98,11 +98,18 @@ struct PrepShared {
   float qc[kPrepThreads];
   unsigned long long red64[kPrepThreads / 32];
   unsigned red32[kPrepThreads / 32];
+  float th0;  // the threshold test's half-width t / 2 in FP32
+  int tlt1;   // t < 1
 };
 
-// Stage an array's FP32 model constants and raster constants (all threads).
+// Stage an array's FP32 model constants and raster constants (all threads);
+// one thread converts the FP64 threshold for the whole block.
 __device__ inline void prep_stage_array(const ArrayDesc& a, PrepShared& sh) {
   stage_consts(&a.md->k, &sh.cs);
+  if (threadIdx.x == 0) {
+    sh.th0 = __double2float_rn(0.5 * a.mt.t);
+    sh.tlt1 = a.mt.t < 1.0 ? 1 : 0;
+  }
   if (a.sc.kind == 0) {
     if (a.rk.valid) {
       if (threadIdx.x < kMaxDot) {
@@ -253,13 +260,16 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
     }
   }
 
-  // (a4) candidate set; the closed doubling loop is team-uniform
+  // (a4) candidate set; the closed doubling loop is team-uniform (its first
+  // pass takes t / 2 and t < 1 from the block's staging, later ones double t
+  // in FP64)
   double tt = a.mt.t;
+  float th = sh.th0;
+  bool tlt1 = sh.tlt1 != 0;
   unsigned mask = 0u;
   int w = -1, base = 0;
   bool amb = false;
   for (int iter = 0; iter < 40; ++iter) {
-    const float th = __double2float_rn(0.5 * tt);
     bool bnd = false;
     if (live) {
       df xi = x;
@@ -270,7 +280,7 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
       amb = fabsf(fr - 0.5f) <= th;
       base = (int)fl + ((!amb && fr >= 0.5f) ? 1 : 0);
       bnd = (xi.hi >= 0.5f - bx && fminf(fr, 1.f - fr) < bx) ||
-            (tt < 1.0 && fabsf(fabsf(fr - 0.5f) - th) < bx);
+            (tlt1 && fabsf(fabsf(fr - 0.5f) - th) < bx);
     }
     if (tballot(bnd)) flags |= kFlagBoundary;
     mask = tballot(live && amb);
@@ -278,12 +288,14 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
     const int sum = tsum_i(live ? base : 0);
     w = nhat - sum;
     if (w >= 0 && w <= __popc(mask)) break;
-    if (tt >= 1.0) {  // impossible in exact arithmetic: settle in FP64
+    if (!tlt1) {  // t = 1 and still infeasible: impossible in exact arithmetic, settle in FP64
       flags |= kFlagBoundary;
       w = w < 0 ? 0 : __popc(mask);
       break;
     }
     tt = (tt <= 0.0) ? 1.0 : fmin(2.0 * tt, 1.0);
+    th = __double2float_rn(0.5 * tt);
+    tlt1 = tt < 1.0;
     flags |= kFlagDoubled;
   }
   if (model_bad) flags |= kFlagUnresolved;
