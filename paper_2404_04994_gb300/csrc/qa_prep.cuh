@@ -107,13 +107,16 @@ __device__ __noinline__ int qp_active_set(int n, const T* Cdd, int ldc,
 // is O(m^2) instead of O(m^3).  Active-set decisions are team ballots.
 // Returns 0 with x_i in lane i, or -1 (no PD system, or no settling within
 // cap iterations).  T = float (prep) or double (FP64 recheck); Cdd has row
-// stride ldc.  Every lane of tmask must call.
+// stride ldc.  Every lane of tmask must call.  Out of line, as is the
+// refinement below: few pixels need the QP, and inlined it spreads the
+// prep's common path over more instruction-cache lines, which the prep
+// shares with the search's walk in the one-kernel form.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float qsqrt(float v) { return sqrtf(v); }
 __device__ __forceinline__ double qsqrt(double v) { return sqrt(v); }
 
 template <typename T, bool CLOSED>
-__device__ __forceinline__ int qp_team(int n, int lt, int TP, unsigned tmask, int tbase,
+__device__ __noinline__ int qp_team(int n, int lt, int TP, unsigned tmask, int tbase,
                                        const T* Cdd, int ldc, const T* v, T s, T ci, T nhat,
                                        unsigned A, T tol, int cap, T (*Ks)[kQPRow], int* alist,
                                        T* zs, T* cs, T& x, unsigned& Afinal) {
@@ -210,7 +213,7 @@ __device__ __forceinline__ int qp_team(int n, int lt, int TP, unsigned tmask, in
 // a free x_i or a multiplier is below -tol (the active set is then in doubt).
 // Every lane of tmask must call; lane i returns x_i (0 for active dots).
 template <bool CLOSED>
-__device__ __forceinline__ int qp_team_refine(int n, int lt, int TP, unsigned tmask, int tbase,
+__device__ __noinline__ int qp_team_refine(int n, int lt, int TP, unsigned tmask, int tbase,
                                               const float* CddHi, const float* CddLo,
                                               const df* v2, df ci, float nhat, unsigned A,
                                               float tol, float (*Ks)[kQPRow], const int* alist,
