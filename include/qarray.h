@@ -388,6 +388,10 @@ int qa_batch_destroy(qa_batch* b);
  * otherwise those of qa_ground_state_open.
  *  - The first call on a device looks up the array's device address (with
  *    that device current); make that first call before any stream capture.
+ *    With CUDA's lazy module loading (the default) that lookup may be what
+ *    loads the library's module on the device, and so what allocates the
+ *    array: make the first call during set-up, where an allocation is
+ *    acceptable; later calls allocate nothing.
  *  - Every call on a device shares the one array, which keeps the previous
  *    call's contents: calls that overlap on the GPU race, so serialise them
  *    (one stream, or events).

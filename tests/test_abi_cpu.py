@@ -44,3 +44,12 @@ def test_last_error_without_gpu():
         api.qa_model_create(np.array([[1.0, 2.0], [2.0, 1.0]]), np.eye(2))
     except api.QAError as e:
         assert e.code in (-4, -7)
+
+
+def test_static_limit_matches_the_header():
+    # the binding's copy of QA_STATIC_MAX_PIXELS follows include/qarray.h
+    from paper_2404_04994_gb300 import api
+    text = open(os.path.join(ROOT, "include", "qarray.h")).read()
+    m = re.search(r"#define\s+QA_STATIC_MAX_PIXELS\s+(\d+)", text)
+    assert m is not None
+    assert int(m.group(1)) == api.STATIC_MAX_PIXELS

@@ -51,6 +51,35 @@ def test_static_entry_matches_open_twice_in_a_row(qa):
     _check(_both(qa, cfg, cfg["raster"], 0.5))
 
 
+def test_static_entry_allocates_nothing(qa):
+    # after one warm-up call (which may load the library's module and with it
+    # the static array), further calls leave the device's free memory as it
+    # was: no cudaMalloc behind the call
+    import torch
+    cfg = inputs.grid16(W=128, H=128)           # exactly QA_STATIC_MAX_PIXELS
+    ras = cfg["raster"]
+    P = ras["W"] * ras["H"]
+    assert P == qa.STATIC_MAX_PIXELS
+    m = qa.Model(cfg["Cdd"], cfg["Cgd"])
+    n_st = torch.empty((P, m.n_dot), dtype=torch.int8, device="cuda")
+    U_st = torch.empty((P,), dtype=torch.float64, device="cuda")
+    f_st = torch.empty((P,), dtype=torch.uint8, device="cuda")
+    ras_c = qa.make_raster(ras, m.n_gate)
+    qa.qa_ground_state_open_static(m.handle, ras_c, 0.5, n_st, U_st, f_st)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        qa.qa_ground_state_open_static(m.handle, ras_c, 0.5, n_st, U_st, f_st)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    # the ordinary call on the same 128 x 128 raster, outside that window
+    n_ref, U_ref, f_ref = m.ground_state_open(ras, threshold=0.5)
+    np.testing.assert_array_equal(n_st.cpu().numpy(), n_ref.cpu().numpy().reshape(P, -1))
+    np.testing.assert_array_equal(f_st.cpu().numpy(), f_ref.cpu().numpy())
+    m.close()
+
+
 def test_static_entry_rejects_oversized_raster(qa):
     import torch
     cfg = inputs.double_dot(W=129, H=128)
