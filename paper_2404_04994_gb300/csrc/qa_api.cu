@@ -162,6 +162,11 @@ void fill_consts(int n, qa::ModelData* md) {
   // square of the FP32 one (per unit of the same scale)
   const double e1 = md->cond * (n + 1) * 5.9604644775390625e-8;
   k.bx_qp_scale2 = (float)(8.0 * e1 * e1);
+  // lower bound of any set of pair terms (the pruned search's bounds)
+  float qn = 0.f;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) qn += std::fmin(0.f, k.Mhi[i * qa::kLdM + j]);
+  k.qneg = qn;
   k.model_bad = md->status != 0;
 }
 
@@ -314,14 +319,20 @@ int select_device(const qa_model* m) {
   return QA_OK;
 }
 
-qa::SearchCfg choose_cfg(int n, double t, long long P, int num_sms) {
+qa::SearchCfg choose_cfg(int n, double t, long long P, int num_sms, bool closed) {
   const double kexp = (t >= 1.0) ? (double)n : (double)n * std::log2(1.0 + t);
   const int ke = (int)std::ceil(kexp - 1e-9);
   qa::SearchCfg c;
   if (n <= 2) c = {2, 0, 1};
   else if (ke <= 4) c = {4, 0, 1};
   else if (ke <= 7) c = {4, 3, 1};
-  else {
+  else if (!closed && ke >= 10) {
+    // open arrays with many ambiguous dots: the pruned search, 16-lane teams
+    // (two pixels per warp), 32 on rasters too small to fill the GPU
+    c = {qa::kBnbL1, qa::kBnbL2, qa::kBnbMinT};
+    if (P * c.T < (long long)num_sms * 128 * 4) c.T = 32;
+    return c;
+  } else {
     c = {5, 4, 1};
     const int rest = ke - 9;
     // two pixels per warp at most: a 16-lane team halves the per-pixel
@@ -501,7 +512,7 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
   a.one.mt.closed = closed ? 1 : 0;
   a.one.mt.n_charges = closed ? n_charges : 0;
   a.one.mt.carrier = m->carrier;
-  a.one.cfg = choose_cfg(m->n, t, P, m->num_sms);
+  a.one.cfg = choose_cfg(m->n, t, P, m->num_sms, closed);
   a.one.klass = qa::search_klass(a.one.cfg);
   a.one.prep_team = prep_team(m->n);
   a.one.rk = raster_constants(m, sc);
@@ -1126,7 +1137,7 @@ extern "C" int qa_ground_state_open_static(qa_model* m, const qa_raster* r,
   a.one.mt.closed = 0;
   a.one.mt.n_charges = 0;
   a.one.mt.carrier = m->carrier;
-  a.one.cfg = choose_cfg(m->n, threshold, P, m->num_sms);
+  a.one.cfg = choose_cfg(m->n, threshold, P, m->num_sms, false);
   a.one.klass = qa::search_klass(a.one.cfg);
   a.one.prep_team = prep_team(m->n);
   a.one.rk = raster_constants(m, sc);
@@ -1205,8 +1216,12 @@ int qa_batch_create(const qa_batch_item* items, int count, qa_batch** out) {
     d.mt.closed = it.closed ? 1 : 0;
     d.mt.n_charges = it.closed ? it.n_charges : 0;
     d.mt.carrier = m->carrier;
-    d.cfg = choose_cfg(m->n, it.threshold, 1LL << 40, m->num_sms);  // no small-raster spreading
+    d.cfg = choose_cfg(m->n, it.threshold, 1LL << 40, m->num_sms,
+                       it.closed != 0);  // no small-raster spreading
     if (it.team) d.cfg.T = it.team;
+    // the pruned search needs teams of kBnbMinT lanes or more
+    if (qa::bnb_search(d.cfg.L1, d.cfg.L2, it.closed != 0) && d.cfg.T < qa::kBnbMinT)
+      d.cfg.T = qa::kBnbMinT;
     d.klass = qa::search_klass(d.cfg);
     d.prep_team = prep_team(m->n);
     d.bx_analytic = 4.0e-7f;
@@ -1268,13 +1283,14 @@ int qa_batch_create(const qa_batch_item* items, int count, qa_batch** out) {
   });
   std::vector<qa::WorkUnit> su_sorted(su.size());
   for (size_t i = 0; i < order.size(); ++i) su_sorted[i] = su[order[i]];
-  int var_first[16] = {}, var_count[16] = {}, var_grid[16] = {}, var_bc[16] = {};
+  int var_first[qa::kBatchVariants] = {}, var_count[qa::kBatchVariants] = {},
+      var_grid[qa::kBatchVariants] = {}, var_bc[qa::kBatchVariants] = {};
   for (size_t i = 0; i < su_sorted.size(); ++i) {
     const int v = variant(su_sorted[i]);
     if (var_count[v]++ == 0) var_first[v] = (int)i;
   }
   int grid_search = 0;
-  for (int v = 0; v < 16; ++v) {
+  for (int v = 0; v < qa::kBatchVariants; ++v) {
     if (!var_count[v]) continue;
     var_bc[v] = grid_search;
     var_grid[v] = std::min(var_count[v], b->num_sms * qa::batch_search_occupancy(v));
@@ -1329,7 +1345,7 @@ int qa_batch_create(const qa_batch_item* items, int count, qa_batch** out) {
   L.bc_search = (qa::BlockCounts*)(mem + off_bcs);
   L.grid_prep = grid_prep;
   L.grid_search = grid_search;
-  for (int v = 0; v < 16; ++v) {
+  for (int v = 0; v < qa::kBatchVariants; ++v) {
     L.var_first[v] = var_first[v];
     L.var_count[v] = var_count[v];
     L.var_grid[v] = var_grid[v];

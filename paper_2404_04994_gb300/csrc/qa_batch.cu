@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_batch(GsLaunch L) {
 // grid over that variant's units, so that every variant runs with its own
 // register count (one kernel over all of them needs the largest).
 template <int L1, int L2, bool CLOSED, bool TF>
-__global__ void __launch_bounds__(kSearchThreads) k_search_batch(GsLaunch L, int v) {
+__device__ __forceinline__ void search_batch_units(const GsLaunch& L, int v) {
   __shared__ SearchShared sh;
   __shared__ int s_unit;
   int staged = -1;
@@ -81,15 +81,31 @@ __global__ void __launch_bounds__(kSearchThreads) k_search_batch(GsLaunch L, int
   }
 }
 
+template <int L1, int L2, bool CLOSED, bool TF>
+__global__ void __launch_bounds__(kSearchThreads) k_search_batch(GsLaunch L, int v) {
+  search_batch_units<L1, L2, CLOSED, TF>(L, v);
+}
+
+// The pruned search's variant (open, 5 + 2 split, teams of kBnbMinT+ lanes),
+// built for kBnbBlocks resident blocks per SM.
+__global__ void __launch_bounds__(kSearchThreads, kBnbBlocks) k_search_batch_bnb(GsLaunch L, int v) {
+  search_batch_units<kBnbL1, kBnbL2, false, true>(L, v);
+}
+
 // The kernel of variant v = 4 klass + 2 closed + team finish.
 typedef void (*BatchSearchKernel)(GsLaunch, int);
 static BatchSearchKernel batch_search_kernel(int v) {
 #define QA_V(l1, l2)                                                                   \
   k_search_batch<l1, l2, false, false>, k_search_batch<l1, l2, false, true>,          \
       k_search_batch<l1, l2, true, false>, k_search_batch<l1, l2, true, true>
-  static const BatchSearchKernel table[16] = {QA_V(2, 0), QA_V(4, 0), QA_V(4, 3), QA_V(5, 4)};
+  static const BatchSearchKernel table[kBatchVariants] = {
+      QA_V(2, 0), QA_V(4, 0), QA_V(4, 3), QA_V(5, 4),
+      k_search_batch<5, 2, false, false>, k_search_batch_bnb,
+      k_search_batch<5, 2, true, false>, k_search_batch<5, 2, true, true>};
+  static_assert(bnb_search(kBnbL1, kBnbL2, false) && kBnbL1 == 5 && kBnbL2 == 2,
+                "variant 4 klass + 1 is the pruned search");
 #undef QA_V
-  return (v >= 0 && v < 16) ? table[v] : nullptr;
+  return (v >= 0 && v < kBatchVariants) ? table[v] : nullptr;
 }
 
 int batch_search_occupancy(int v) {
@@ -101,12 +117,13 @@ int batch_search_occupancy(int v) {
 }
 
 // Resident blocks per SM of the persistent prep kernel and of the search of
-// the widest variant (open, 5 + 4 split, team finish), for unit sizing.
+// the large open arrays' variant (the pruned search, 5 + 2 split, team
+// finish), for unit sizing.
 void batch_occupancy(int* prep_per_sm, int* search_per_sm) {
   *prep_per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(prep_per_sm, k_prep_batch, kPrepThreads, 0);
   if (*prep_per_sm < 1) *prep_per_sm = 1;
-  *search_per_sm = batch_search_occupancy(4 * 3 + 1);
+  *search_per_sm = batch_search_occupancy(4 * 4 + 1);
 }
 
 cudaError_t launch_ground_state_batch(const GsLaunch& L, cudaStream_t st) {
@@ -114,7 +131,7 @@ cudaError_t launch_ground_state_batch(const GsLaunch& L, cudaStream_t st) {
   cudaMemsetAsync(L.cnt, 0, sizeof(Counters), st);
   k_prep_batch<<<L.grid_prep, kPrepThreads, 0, st>>>(L);
   if (L.ev) cudaEventRecord(L.ev[1], st);
-  for (int v = 0; v < 16; ++v)
+  for (int v = 0; v < kBatchVariants; ++v)
     if (L.var_count[v] > 0) batch_search_kernel(v)<<<L.var_grid[v], kSearchThreads, 0, st>>>(L, v);
   if (L.ev) cudaEventRecord(L.ev[2], st);
   launch_lists(L, st);

@@ -109,7 +109,8 @@ struct __align__(16) ModelConsts {
   df sv2[kMaxDot];             // Cdd 1 as double-float
   float absl[kMaxDot];         // M_ii / 2 + sum_{j < i} |M_ij| (FP32 hi parts, j increasing)
   float bx_qp_scale2;          // ... after one double-float refinement of the QP
-  int pad2[3];
+  float qneg;                  // sum of the negative off-diagonal M_ij, i < j (0 for Maxwell Cdd)
+  int pad2[2];
 };
 
 // Device copy of a model (written by the host or by the Cholesky kernel).
@@ -156,7 +157,7 @@ struct Counters {
   unsigned int n_tie;   // length of the near-tie list
   unsigned int q_prep;  // batched launch: work-queue heads
   unsigned int q_search;
-  unsigned int q_var[16];  // batched launch: the search queue of each kernel variant
+  unsigned int q_var[20];  // batched launch: the search queue of each kernel variant
   unsigned int lists_done; // blocks of the FP64 recheck kernel that have finished
 };
 

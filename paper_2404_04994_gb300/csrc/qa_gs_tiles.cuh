@@ -371,7 +371,12 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
     rec->w = (signed char)(CLOSED ? w : -1);
     rec->flags = (unsigned char)flags;
     rec->qpA = (unsigned short)qp_set;
-    rec->bound = near_tie_bound(S, k, a.cfg.L2);
+    // the pruned search walks a shallower middle level than the resolve's
+    // re-walk (kCheckL2), which shortlists by this bound, and forms each
+    // rest state from up to kBnbItBits + 2 more table sums
+    rec->bound = bnb_search(a.cfg.L1, a.cfg.L2, CLOSED)
+                     ? near_tie_bound(S, k, max(a.cfg.L2, kCheckL2), kBnbItBits + 2)
+                     : near_tie_bound(S, k, a.cfg.L2);
     my_cand = CLOSED ? binom(k, w) : (1ull << k);
     my_qp = (flags & kFlagQP) ? 1u : 0u;
     my_doubled = (flags & kFlagDoubled) ? 1u : 0u;
@@ -393,13 +398,39 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
 // ---------------------------------------------------------------------------
 // search stage: shared state of a block
 // ---------------------------------------------------------------------------
+// Three layouts share the space: teams narrower than kTeamFinishMin keep a
+// slot table per thread; block-level teams one per team with their walk
+// tables; the pruned search (teams of kBnbMinT+ lanes) its bound tables.
+constexpr int kTeamsTF = kSearchThreads / kTeamFinishMin;
+constexpr int kTeamsBnb = kSearchThreads / kBnbMinT;
 struct SearchShared {
   ModelConsts cs;
-  int sdot[kSearchThreads][kMaxDot];
-  float sh[kSearchThreads][kMaxDot];
-  __align__(16) float colt[kSearchThreads / kTeamFinishMin][4 * kColStride];
-  __align__(16) float itab[kSearchThreads / kTeamFinishMin][(1 << kItMax) * kItStride];
-  __align__(16) float cslot[kSearchThreads][kItMax];
+  union {
+    struct {
+      int sdot[kSearchThreads][kMaxDot];
+      float sh[kSearchThreads][kMaxDot];
+    } lane;
+    struct {
+      int sdot[kTeamsTF][kMaxDot];
+      float sh[kTeamsTF][kMaxDot];
+      __align__(16) float colt[kTeamsTF][4 * kColStride];
+      __align__(16) float itab[kTeamsTF][(1 << kItMax) * kItStride];
+      __align__(16) float cslot[kSearchThreads][kItMax];
+    } team;
+    struct {
+      int sdot[kTeamsBnb][kMaxDot];
+      float sh[kTeamsBnb][kMaxDot];
+      int slot_of[kTeamsBnb][kMaxDot];  // slot of each ambiguous dot
+      float pm[kTeamsBnb][kMaxDot * kLdM];
+      float vv[kTeamsBnb][kMaxDot];
+      __align__(16) float itab[kTeamsBnb][(1 << kBnbItBits) * kBnbStride];
+      __align__(16) float ltab[kSearchThreads][kBnbLane];
+      __half lb[kTeamsBnb][kBnbStates];
+      unsigned short rbuf[kTeamsBnb][kBnbBuf];
+      float rlb[kTeamsBnb][kBnbBuf];
+      __align__(16) float ptab[kTeamsBnb][1 << kBnbL1];
+    } bnb;
+  } u;
   unsigned long long red64[kSearchThreads / 32];
   unsigned red32[kSearchThreads / 32];
 };
@@ -441,35 +472,77 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
   const PixRec* rec = a.recs + (active ? p : 0);
   const unsigned mask = active ? rec->mask : 0u;
   const int k = __popc(mask);
-  // slot table of the pixel: slot s = the s-th ambiguous dot (lanes in parallel)
-  if (active)
+  // BNB: the pruned search (open, 5 + 2 split, teams of kBnbMinT+ lanes,
+  // which the host guarantees for this split)
+  constexpr bool BNB = TF && bnb_search(L1, L2, CLOSED);
+  int* sdot = BNB ? sh.u.bnb.sdot[team] : TF ? sh.u.team.sdot[team] : sh.u.lane.sdot[team];
+  float* sht = BNB ? sh.u.bnb.sh[team] : TF ? sh.u.team.sh[team] : sh.u.lane.sh[team];
+  int* slot_of = BNB ? sh.u.bnb.slot_of[team] : nullptr;
+  if (BNB) {
+    // slot s = the ambiguous dot of rank s by |h_i + M_ii / 2|, ascending
+    // (ties by dot index): the least certain dots are walked, the most
+    // certain ones are the outer slots the bounds prune
+    if (active)
+      for (int i = lt; i < n; i += T)
+        sht[i] = ((mask >> i) & 1u) ? fabsf(rec->h[i] + 0.5f * sM[i * kLdM + i]) : 0.f;
+    __syncwarp();
+    int rank = -1;
+    if (active && lt < n && ((mask >> lt) & 1u)) {
+      const float key = sht[lt];
+      rank = 0;
+      for (int j = 0; j < n; ++j) {
+        const float kj = sht[j];
+        rank += (((mask >> j) & 1u) && (kj < key || (kj == key && j < lt))) ? 1 : 0;
+      }
+    }
+    __syncwarp();
+    if (rank >= 0) {
+      sdot[rank] = lt;
+      sht[rank] = rec->h[lt];
+      slot_of[lt] = rank;
+    }
+  } else if (active) {
+    // slot table of the pixel: slot s = the s-th ambiguous dot (lanes in parallel)
     for (int i = lt; i < n; i += T)
       if ((mask >> i) & 1u) {
         const int s = __popc(mask & ((1u << i) - 1u));
-        sh.sdot[team][s] = i;
-        sh.sh[team][s] = rec->h[i];
+        sdot[s] = i;
+        sht[s] = rec->h[i];
       }
+  }
   __syncwarp();
   float m1 = kInf, m2 = kInf;
   unsigned b1 = 0u;
   unsigned long long ev = 0;
-  const SlotView sv{sh.sdot[team], sh.sh[team], active ? k : 0, active ? (int)rec->w : -1};
+  const SlotView sv{sdot, sht, active ? k : 0, active ? (int)rec->w : -1};
   // TF (teams of 8 or more lanes): search at block level and finish the
   // winning block together; smaller teams finish each lane's best block in
   // the lane.
-  float* colt = TF ? sh.colt[team] : nullptr;
-  if (TF) {
+  float* colt = (TF && !BNB) ? sh.u.team.colt[team] : nullptr;
+  float* itab = (TF && !BNB) ? sh.u.team.itab[team] : nullptr;
+  if (TF && !BNB) {
     static_assert(L2 <= 4 && L1 + L2 <= kColStride, "column table layout");
     if (active) {
       col_build<L1, L2>(sM, sv, lt, T, colt);
-      if (L1 + L2 >= 9) iter_build<L1, L2>(sM, sv, lt, T, sh.itab[team]);
+      if (L1 + L2 >= 9) iter_build<L1, L2>(sM, sv, lt, T, itab);
     }
     __syncwarp();
   }
-  if (active)
-    search_lane<L1, L2, CLOSED, false, TF>(sM, sv, lt, T, 0.f, nullptr, nullptr, 0u, m1, b1,
-                                           m2, ev, colt, TF ? sh.itab[team] : nullptr,
-                                           sh.cslot[threadIdx.x]);
+  if (active) {
+    if constexpr (BNB) {
+      const unsigned wl = threadIdx.x & 31u;
+      const unsigned tmask =
+          T >= 32 ? kFull : (((1u << T) - 1u) << (wl & ~(unsigned)(T - 1)));
+      search_bnb(sM, sv, lt, T, tmask, rec->bound, sh.cs.qneg, sh.u.bnb.pm[team],
+                 sh.u.bnb.vv[team], sh.u.bnb.itab[team],
+                 sh.u.bnb.ltab[team * T], sh.u.bnb.lb[team], sh.u.bnb.rbuf[team],
+                 sh.u.bnb.rlb[team], sh.u.bnb.ptab[team], m1, b1, m2, ev);
+    } else {
+      search_lane<L1, L2, CLOSED, false, TF>(sM, sv, lt, T, 0.f, nullptr, nullptr, 0u, m1, b1,
+                                             m2, ev, colt, itab,
+                                             TF ? sh.u.team.cslot[threadIdx.x] : nullptr);
+    }
+  }
   // best (block or candidate) with its id, and the second-best minimum
   for (int off = 1; off < T; off <<= 1) {
     const float om1 = __shfl_xor_sync(kFull, m1, off);
@@ -501,12 +574,15 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
   df u = {0.f, 0.f};
   unsigned flags = 0u;
   __syncwarp();
-  float* rhi = sh.sh[team];
-  int* rlo = sh.sdot[team];
+  float* rhi = sht;
+  int* rlo = sdot;
   if (active) {
     for (int i = lt; i < n; i += T) {
       int ni = rec->base[i];
-      if ((mask >> i) & 1u) ni += (int)((b1 >> __popc(mask & ((1u << i) - 1u))) & 1u);
+      if ((mask >> i) & 1u) {
+        const int si = BNB ? slot_of[i] : __popc(mask & ((1u << i) - 1u));
+        ni += (int)((b1 >> si) & 1u);
+      }
       const df ri = df_sub({(float)ni, 0.f}, {rec->chi[i], rec->clo[i]});
       rhi[i] = ri.hi;
       rlo[i] = __float_as_int(ri.lo);

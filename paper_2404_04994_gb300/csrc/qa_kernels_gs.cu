@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(GsLaunch L) {
 // L1 / L2 for the search), so no grid-wide wait separates the two stages and
 // the prep of later tiles overlaps the search of earlier ones.
 template <int L1, int L2, bool CLOSED, bool TF>
-__global__ void __launch_bounds__(kSearchThreads) k_ground_state(GsLaunch L) {
+__device__ __forceinline__ void ground_state_tile(const GsLaunch& L) {
   __shared__ GsShared sh;
   const ArrayDesc& a = L.one;
   // the resolve may launch once every block has passed here (all are then
@@ -66,11 +66,21 @@ __global__ void __launch_bounds__(kSearchThreads) k_ground_state(GsLaunch L) {
   }
 }
 
+template <int L1, int L2, bool CLOSED, bool TF>
+__global__ void __launch_bounds__(kSearchThreads) k_ground_state(GsLaunch L) {
+  ground_state_tile<L1, L2, CLOSED, TF>(L);
+}
+
+// The pruned search's tiles, built for kBnbBlocks resident blocks per SM.
+__global__ void __launch_bounds__(kSearchThreads, kBnbBlocks) k_ground_state_bnb(GsLaunch L) {
+  ground_state_tile<kBnbL1, kBnbL2, false, true>(L);
+}
+
 // Search alone, behind k_prep (programmatic dependent launch): for tilings
 // where one search block covers several prep blocks' pixels, which a block
 // preparing its own tile would prepare one pass after another.
 template <int L1, int L2, bool CLOSED, bool TF>
-__global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch L) {
+__device__ __forceinline__ void search_only_tile(const GsLaunch& L) {
   __shared__ SearchShared sh;
   const ArrayDesc& a = L.one;
   stage_consts(&a.md->k, &sh.cs);
@@ -89,6 +99,15 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch L) {
     o.boundary = acc.boundary;
     o.overflow = acc.overflow;
   }
+}
+
+template <int L1, int L2, bool CLOSED, bool TF>
+__global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch L) {
+  search_only_tile<L1, L2, CLOSED, TF>(L);
+}
+
+__global__ void __launch_bounds__(kSearchThreads, kBnbBlocks) k_search_bnb(GsLaunch L) {
+  search_only_tile<kBnbL1, kBnbL2, false, true>(L);
 }
 
 // Near-tie list: one block per entry, grid-stride.  In a batched call the
@@ -212,10 +231,16 @@ static cudaError_t run(const GsLaunch& L, cudaStream_t st) {
   // on entry; resolve and recheck start early behind their predecessor
   cudaError_t e = cudaSuccess;
   if (L.ev) cudaEventRecord(L.ev[0], st);
+  // the pruned search (5 + 2 split, open; teams of kBnbMinT+ lanes) has
+  // kernels of its own, built for kBnbBlocks resident blocks per SM
+  constexpr bool kBnb = bnb_search(L1, L2, CLOSED);
+  const bool tf = L.one.cfg.T >= kTeamFinishMin;
   if (fused_tiles(L)) {
     if (L.ev) cudaEventRecord(L.ev[1], st);
-    if (L.one.cfg.T >= kTeamFinishMin)
-      k_ground_state<L1, L2, CLOSED, true><<<search_blocks(L), kSearchThreads, 0, st>>>(L);
+    if (kBnb && tf)
+      k_ground_state_bnb<<<search_blocks(L), kSearchThreads, 0, st>>>(L);
+    else if (tf)
+      k_ground_state<L1, L2, CLOSED, !kBnb><<<search_blocks(L), kSearchThreads, 0, st>>>(L);
     else
       k_ground_state<L1, L2, CLOSED, false><<<search_blocks(L), kSearchThreads, 0, st>>>(L);
     e = cudaGetLastError();
@@ -224,8 +249,10 @@ static cudaError_t run(const GsLaunch& L, cudaStream_t st) {
     e = cudaGetLastError();
     if (L.ev) cudaEventRecord(L.ev[1], st);
     if (e == cudaSuccess) {
-      if (L.one.cfg.T >= kTeamFinishMin)
-        e = launch_dependent(k_search<L1, L2, CLOSED, true>, (unsigned)search_blocks(L),
+      if (kBnb && tf)
+        e = launch_dependent(k_search_bnb, (unsigned)search_blocks(L), kSearchThreads, st, L);
+      else if (tf)
+        e = launch_dependent(k_search<L1, L2, CLOSED, !kBnb>, (unsigned)search_blocks(L),
                              kSearchThreads, st, L);
       else
         e = launch_dependent(k_search<L1, L2, CLOSED, false>, (unsigned)search_blocks(L),
@@ -253,7 +280,7 @@ cudaError_t launch_prep(const GsLaunch& L, cudaStream_t st) {
 
 int search_klass(const SearchCfg& c) {
   const int key = c.L1 * 10 + c.L2;
-  return key == 20 ? 0 : key == 40 ? 1 : key == 43 ? 2 : key == 54 ? 3 : -1;
+  return key == 20 ? 0 : key == 40 ? 1 : key == 43 ? 2 : key == 54 ? 3 : key == 52 ? 4 : -1;
 }
 
 bool search_cfg_supported(const SearchCfg& c) {
@@ -268,6 +295,7 @@ cudaError_t launch_ground_state(const GsLaunch& L, cudaStream_t st) {
     case 1: return cl ? run<4, 0, true>(L, st) : run<4, 0, false>(L, st);
     case 2: return cl ? run<4, 3, true>(L, st) : run<4, 3, false>(L, st);
     case 3: return cl ? run<5, 4, true>(L, st) : run<5, 4, false>(L, st);
+    case 4: return cl ? run<5, 2, true>(L, st) : run<5, 2, false>(L, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -38,6 +38,18 @@ struct ArrayDesc {
 
 constexpr int kSearchThreads = 128;  // threads of a search block
 constexpr int kTeamFinishMin = 8;    // teams at least this wide finish the winning block together
+// The pruned search (branch and bound over the outer slots, qa_search.cuh):
+// open arrays with the 5 + 2 split, teams of kBnbMinT or 32 lanes.
+constexpr int kBnbL1 = 5, kBnbL2 = 2;
+constexpr int kBnbMinT = 16;
+constexpr int kBnbBlocks = 5;  // resident blocks per SM its kernels are built for
+// Batched search kernel variants: 4 per split class (closed, team finish).
+constexpr int kBatchVariants = 20;
+static_assert(sizeof(((Counters*)nullptr)->q_var) / sizeof(unsigned) == kBatchVariants,
+              "one queue head per batched search variant");
+__host__ __device__ constexpr bool bnb_search(int L1, int L2, bool closed) {
+  return !closed && L1 == kBnbL1 && L2 == kBnbL2;
+}
 
 // Pixels [first, first + count) of one array of a batched call.
 struct WorkUnit {
@@ -63,7 +75,8 @@ struct GsLaunch {
   // 2 closed + team finish (units [var_first, var_first + var_count) of
   // search_units, largest first within a group), one persistent grid of
   // var_grid blocks per variant, its block counts from bc_search + var_bc
-  int var_first[16], var_count[16], var_grid[16], var_bc[16];
+  int var_first[kBatchVariants], var_count[kBatchVariants], var_grid[kBatchVariants],
+      var_bc[kBatchVariants];
   int num_sms;
   cudaEvent_t* ev;     // optional: events around prep / search / resolve+recheck
 };

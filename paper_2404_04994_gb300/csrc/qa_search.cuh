@@ -25,7 +25,10 @@
 // argmin and the in-block runner-up.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "qa_device.cuh"
+#include "qa_launch.h"
 
 namespace qa {
 
@@ -62,6 +65,44 @@ __device__ __forceinline__ float inner_min_open(float A, const float* q,
     if (b + 2 < NI) {
       float2 f = fadd2(make_float2(S[b + 2], S[b + 3]),
                        make_float2(P[b + 2], P[b + 3]));
+      m1 = fmin3(m1, f.x, f.y);
+    }
+  }
+  return fminf(m0, m1);
+}
+
+// The same with the pair table P in shared memory (16-byte aligned; the
+// team's lanes read the same entries, so the loads are broadcasts).
+template <int L1>
+__device__ __forceinline__ float inner_min_open_smem(float A, const float* q,
+                                                     const float* __restrict__ P) {
+  constexpr int NI = 1 << L1;
+  static_assert(NI >= 8, "four-entry chunks");
+  float S[NI];
+  S[0] = A;
+  S[1] = __fadd_rn(A, q[0]);
+#pragma unroll
+  for (int j = 1; j < L1; ++j) {
+    const float2 qq = make_float2(q[j], q[j]);
+#pragma unroll
+    for (int b = 0; b < (1 << j); b += 2) {
+      float2 r = fadd2(make_float2(S[b], S[b + 1]), qq);
+      S[b + (1 << j)] = r.x;
+      S[b + 1 + (1 << j)] = r.y;
+    }
+  }
+  const float4* P4 = reinterpret_cast<const float4*>(P);
+  float m0 = fminf(S[0], S[1]);
+  float m1 = kInf;
+#pragma unroll
+  for (int b = 0; b < NI; b += 4) {
+    const float4 p = P4[b / 4];
+    if (b == 0) {
+      m1 = fminf(__fadd_rn(S[2], p.z), __fadd_rn(S[3], p.w));
+    } else {
+      const float2 e = fadd2(make_float2(S[b], S[b + 1]), make_float2(p.x, p.y));
+      const float2 f = fadd2(make_float2(S[b + 2], S[b + 3]), make_float2(p.z, p.w));
+      m0 = fmin3(m0, e.x, e.y);
       m1 = fmin3(m1, f.x, f.y);
     }
   }
@@ -589,6 +630,344 @@ __device__ __forceinline__ void team_finish(const float* __restrict__ sM, const 
   bits1 = Sbits | (bb == 0xffffffffu ? 0u : bb);
 }
 
+// ---------------------------------------------------------------------------
+// Pruned search: open arrays, teams of 16 or 32 lanes, split L1 = 5, L2 = 2.
+// An exact branch and bound over the outer slots.
+//
+// With the inner and middle slots x (L1 + L2 of them) free and the outer
+// pattern o fixed, a candidate's energy is
+//     E(o, x) = A_o + sum_j L_oj x_j + Q(x),
+// A_o the energy of o alone, L_oj = h_j + M_jj / 2 + sum_{s in o} M_js, and
+// Q(x) the pair terms among the set bits of x.  Q(x) is at least qneg, the
+// sum of the model's negative pair terms (0 whenever M is entrywise
+// non-negative, as for every Maxwell Cdd, whose inverse is non-negative), so
+//     LB_o = A_o + sum_j min(0, L_oj) + qneg
+// bounds every candidate of o from below.  An outer pattern whose bound lies
+// above an energy already known to be at least the runner-up (plus the FP32
+// error margin) holds neither the argmin nor the runner-up: it is skipped,
+// and the top two over the candidate set are exactly those over the patterns
+// walked.  The slots come ordered so that the outer ones are the dots whose
+// single-flip energy at the base, h_s + M_ss / 2, is largest in magnitude:
+// a wrong setting of such a dot costs most, so its patterns are pruned first.
+//
+// Lane t of the team owns the outer patterns o = t + T i.  It bounds them
+// all, and walks the one with the lowest bound first (every owning lane at
+// once), which usually finds the argmin and a runner-up close to it; the cut
+// is then the team's second-best block minimum, and the few patterns whose
+// bound is still below it are collected once and walked in rounds of T, the
+// cut tightening after every round.
+// ---------------------------------------------------------------------------
+constexpr int kBnbIn = kBnbL1 + kBnbL2;   // walked slots per outer pattern
+constexpr int kBnbItBits = 5;             // iteration bits at most (k = 16, T = 16)
+constexpr int kBnbStride = 8;             // iteration-table row: A part, L parts
+constexpr int kBnbLane = 16;              // lane-table row: At, Lt[kBnbIn], cross[kBnbItBits]
+constexpr int kBnbStates = 1 << (kMaxDot - kBnbIn);
+constexpr int kBnbBuf = 64;               // patterns collected per pass
+
+// Team-cooperative tables of the pruned search (lane lt of T; sync after):
+//   pm[s][s'] = M(dot_s, dot_s') for slots s, s' < k (kLdM stride, 0 beyond)
+//   vv[s]     = h_s + M_ss / 2 (slots beyond k: kBig for an inner slot, so
+//               that no pattern using it wins, 0 otherwise)
+// built with independent loads (one slot row per lane), so that the tables
+// that follow read slot pairs directly instead of through the dot indices.
+__device__ __forceinline__ void bnb_pair_build(const float* sM, const SlotView& sv, int lt, int T,
+                                               float* pm, float* vv) {
+  const int k = sv.k;
+  for (int r = lt; r < kMaxDot; r += T) {
+    const bool live = r < k;
+    const int dr = live ? sv.dot[r] : 0;
+    const float* Mrow = sM + dr * kLdM;
+    float row[kMaxDot];
+#pragma unroll
+    for (int c = 0; c < kMaxDot; ++c) {
+      const int dc = (live && c < k) ? sv.dot[c] : 0;
+      row[c] = (live && c < k) ? Mrow[dc] : 0.f;
+    }
+#pragma unroll
+    for (int c = 0; c < kMaxDot; ++c) pm[r * kLdM + c] = row[c];
+    vv[r] = live ? sv.h[r] + 0.5f * Mrow[dr] : (r < kBnbL1 ? kBig : 0.f);
+  }
+}
+
+// Team-cooperative iteration table (lane lt of T; sync after): for each
+// pattern i of the nit iteration slots (slots kBnbIn + nlb + ii), the energy
+// of its set slots alone (v and their pairs, at 0) and, at 1 + j, the sum of
+// M(slot j, s) over its set slots s for every walked slot j (0 for j >= k).
+// Fixed-range 0 / 1-weighted sums over the pair table.
+__device__ __forceinline__ void bnb_iter_build(const float* pm, const float* vv, int lt, int T,
+                                               int nlb, int nit, float* itab) {
+  const int s0 = kBnbIn + nlb;
+  for (int it = lt; it < (1 << nit); it += T) {
+    float w[kBnbItBits];
+#pragma unroll
+    for (int ii = 0; ii < kBnbItBits; ++ii) w[ii] = (ii < nit && ((it >> ii) & 1)) ? 1.f : 0.f;
+    float A = 0.f;
+#pragma unroll
+    for (int ii = 0; ii < kBnbItBits; ++ii) {
+      const int si = min(s0 + ii, kMaxDot - 1);
+      float add = vv[si];
+#pragma unroll
+      for (int i2 = 0; i2 < ii; ++i2) add = fmaf(w[i2], pm[si * kLdM + min(s0 + i2, kMaxDot - 1)], add);
+      A = fmaf(w[ii], add, A);
+    }
+    float row[kBnbStride];
+    row[0] = A;
+#pragma unroll
+    for (int j = 0; j < kBnbIn; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int ii = 0; ii < kBnbItBits; ++ii)
+        acc = fmaf(w[ii], pm[j * kLdM + min(s0 + ii, kMaxDot - 1)], acc);
+      row[1 + j] = acc;
+    }
+    float4* dst = reinterpret_cast<float4*>(itab + it * kBnbStride);
+    dst[0] = make_float4(row[0], row[1], row[2], row[3]);
+    dst[1] = make_float4(row[4], row[5], row[6], row[7]);
+  }
+}
+
+// The team-wide top two of per-lane (a1 <= a2) pairs, by shuffles over the
+// team's lanes (tmask, width T); every lane ends with the same pair.
+__device__ __forceinline__ void team_top2(unsigned tmask, int T, float& a1, float& a2) {
+  for (int off = 1; off < T; off <<= 1) {
+    const float o1 = __shfl_xor_sync(tmask, a1, off, T);
+    const float o2 = __shfl_xor_sync(tmask, a2, off, T);
+    a2 = fminf(fminf(a2, o2), fmaxf(a1, o1));
+    a1 = fminf(a1, o1);
+  }
+}
+
+// Rest state of outer pattern o from the team tables: the lane part of its
+// lane bits, the iteration part of its iteration bits, and their pair terms.
+__device__ __forceinline__ void bnb_rest(const float* ltab, const float* itab, int nlb, int o,
+                                         float& A, float* L) {
+  const float4* lp = reinterpret_cast<const float4*>(ltab + (o & ((1 << nlb) - 1)) * kBnbLane);
+  const float4* ip = reinterpret_cast<const float4*>(itab + (o >> nlb) * kBnbStride);
+  const float4 l0 = lp[0], l1 = lp[1], l2 = lp[2], l3 = lp[3];
+  const float4 i0 = ip[0], i1 = ip[1];
+  const unsigned i = (unsigned)(o >> nlb);
+  const float cr[kBnbItBits] = {l2.x, l2.y, l2.z, l2.w, l3.x};
+  float x = 0.f;
+#pragma unroll
+  for (int ii = 0; ii < kBnbItBits; ++ii) x = fmaf(((i >> ii) & 1u) ? 1.f : 0.f, cr[ii], x);
+  A = (l0.x + x) + i0.x;
+  L[0] = l0.y + i0.y;
+  L[1] = l0.z + i0.z;
+  L[2] = l0.w + i0.w;
+  L[3] = l1.x + i1.x;
+  L[4] = l1.y + i1.y;
+  L[5] = l1.z + i1.z;
+  L[6] = l1.w + i1.w;
+}
+
+// Pruned search of one pixel by its team (every lane of the team calls it,
+// lane lt of T, tmask the team's lanes).  Results per lane, for the team's
+// top-two merge and team_finish: the lane's best block minimum m1 with its
+// block id b1 = (o << L2) | middle pattern, and its second-best block
+// minimum m2.  bound: the pixel's FP32 error bound (the cut's margin);
+// qneg: the model's lower bound of any pair-term sum.  pm, vv, itab, ltab,
+// lb, rbuf: the team's shared tables (kMaxDot x kLdM slot pairs, kMaxDot
+// single-flip energies, (1 << kBnbItBits) kBnbStride-rows, a kBnbLane-row per
+// lane, kBnbStates FP16 bounds, kBnbBuf collected patterns and their bounds,
+// 2^L1 inner pair terms, 16-byte aligned).
+__device__ __forceinline__ void search_bnb(const float* __restrict__ sM, const SlotView sv,
+                                           int lt, int T, unsigned tmask, float bound,
+                                           float qneg, float* pm, float* vv, float* itab,
+                                           float* ltab, __half* lb, unsigned short* rbuf,
+                                           float* rlb, float* ptab,
+                                           float& m1, unsigned& b1, float& m2,
+                                           unsigned long long& evaluated) {
+  constexpr int L1 = kBnbL1, L2 = kBnbL2, NI = 1 << L1, NM = 1 << L2;
+  static_assert(kBnbIn == 7 && kBnbStride == 8 && kBnbLane >= 1 + kBnbIn + kBnbItBits,
+                "pruned-search table layout");
+  const int k = sv.k;
+  const int nmid = min(max(k - L1, 0), L2);
+  const int nout = max(k - kBnbIn, 0);
+  const int nlb = min(__ffs(T) - 1, nout);
+  const int nit = nout - nlb;
+  const int nsteps = 1 << nmid;
+  const bool own = lt < (1 << nlb);
+
+  // team tables: slot pairs and single-flip energies first, then the
+  // iteration slots' terms and each owning lane's lane-bit part with its pair
+  // terms with every iteration slot (fixed-range 0 / 1-weighted sums, the same
+  // trip count in every lane)
+  bnb_pair_build(sM, sv, lt, T, pm, vv);
+  __syncwarp(tmask);
+  bnb_iter_build(pm, vv, lt, T, nlb, nit, itab);
+  float At = 0.f, Lt[kBnbIn], cr[kBnbItBits];
+#pragma unroll
+  for (int j = 0; j < kBnbIn; ++j) Lt[j] = vv[j];
+#pragma unroll
+  for (int ii = 0; ii < kBnbItBits; ++ii) cr[ii] = 0.f;
+  if (own) {
+    constexpr int kLB = 5;  // lane bits at most (T <= 32)
+    float wO[kLB];
+#pragma unroll
+    for (int i = 0; i < kLB; ++i) wO[i] = (i < nlb && ((lt >> i) & 1)) ? 1.f : 0.f;
+#pragma unroll
+    for (int i = 0; i < kLB; ++i) {
+      const int si = min(kBnbIn + i, kMaxDot - 1);
+      const float* prow = pm + si * kLdM;
+      float add = vv[si];
+#pragma unroll
+      for (int i2 = 0; i2 < i; ++i2) add = fmaf(wO[i2], prow[kBnbIn + i2], add);
+      At = fmaf(wO[i], add, At);
+#pragma unroll
+      for (int j = 0; j < kBnbIn; ++j) Lt[j] = fmaf(wO[i], prow[j], Lt[j]);
+#pragma unroll
+      for (int ii = 0; ii < kBnbItBits; ++ii)
+        cr[ii] = fmaf((ii < nit) ? wO[i] : 0.f, prow[min(kBnbIn + nlb + ii, kMaxDot - 1)], cr[ii]);
+    }
+    float4* my = reinterpret_cast<float4*>(ltab + lt * kBnbLane);
+    my[0] = make_float4(At, Lt[0], Lt[1], Lt[2]);
+    my[1] = make_float4(Lt[3], Lt[4], Lt[5], Lt[6]);
+    my[2] = make_float4(cr[0], cr[1], cr[2], cr[3]);
+    my[3] = make_float4(cr[4], 0.f, 0.f, 0.f);
+  }
+  __syncwarp(tmask);
+
+  // bounds of the lane's own outer patterns (all 2^kBnbItBits rows are read:
+  // rows past 2^nit hold garbage that the masks below drop), and the lowest
+  const int nst = own ? (1 << nit) : 0;
+  float lbest = kInf;
+  int ibest = 0;
+#pragma unroll
+  for (int i = 0; i < (1 << kBnbItBits); ++i) {
+    const float4* ip = reinterpret_cast<const float4*>(itab + i * kBnbStride);
+    const float4 i0 = ip[0], i1 = ip[1];
+    float x = 0.f;
+#pragma unroll
+    for (int ii = 0; ii < kBnbItBits; ++ii)
+      if ((i >> ii) & 1) x += cr[ii];
+    const float A = (At + x) + i0.x;
+    const float s0 = fminf(0.f, Lt[0] + i0.y) + fminf(0.f, Lt[1] + i0.z);
+    const float s1 = fminf(0.f, Lt[2] + i0.w) + fminf(0.f, Lt[3] + i1.x);
+    const float s2 = fminf(0.f, Lt[4] + i1.y) + fminf(0.f, Lt[5] + i1.z);
+    const float s3 = fminf(0.f, Lt[6] + i1.w);
+    const float v = (A + ((s0 + s1) + (s2 + s3))) + qneg;
+    // stored rounded down to FP16: still a lower bound, half the space
+    if (i < nst) lb[lt | (i << nlb)] = __float2half_rd(v);
+    const bool better = i < nst && v < lbest;
+    lbest = better ? v : lbest;
+    ibest = better ? i : ibest;
+  }
+
+  // the walk of one outer pattern: its 2^nmid middle states, each with the
+  // inner table evaluated by doubling (inner_min_open)
+  // the inner pair table P[b] = sum_{j < l in b} M(j, l), one entry per
+  // lane at a time into the team's shared row (fixed-range 0 / 1 weights)
+  for (int b = lt; b < NI; b += T) {
+    float r = 0.f;
+#pragma unroll
+    for (int j = 1; j < L1; ++j)
+#pragma unroll
+      for (int l = 0; l < j; ++l)
+        r = fmaf((((b >> j) & 1) && ((b >> l) & 1)) ? 1.f : 0.f, pm[j * kLdM + l], r);
+    ptab[b] = r;
+  }
+  float Mmm[L2][L2], Mim[L1][L2];
+#pragma unroll
+  for (int m = 0; m < L2; ++m)
+#pragma unroll
+    for (int m2 = 0; m2 < L2; ++m2)
+      Mmm[m][m2] = (m != m2 && m < nmid && m2 < nmid) ? pm[(L1 + m) * kLdM + L1 + m2] : 0.f;
+#pragma unroll
+  for (int j = 0; j < L1; ++j)
+#pragma unroll
+    for (int m = 0; m < L2; ++m)
+      Mim[j][m] = (m < nmid) ? pm[j * kLdM + L1 + m] : 0.f;
+  float g1 = kInf, g2 = kInf;
+  unsigned blk = 0u;
+  unsigned long long ev = 0;
+  auto walk = [&](int o) {
+    float A, L[kBnbIn];
+    bnb_rest(ltab, itab, nlb, o, A, L);
+    float q[L1], gm[L2];
+#pragma unroll
+    for (int j = 0; j < L1; ++j) q[j] = L[j];
+#pragma unroll
+    for (int m = 0; m < L2; ++m) gm[m] = L[L1 + m];
+    const unsigned obase = (unsigned)o << L2;
+#pragma unroll
+    for (int s = 0; s < NM; ++s) {
+      if (s >= nsteps) continue;
+      if (s > 0) {
+        const int mb = ctz_c((unsigned)s);
+        const bool up = (gray_c((unsigned)s) >> mb) & 1u;
+        A = up ? A + gm[mb] : A - gm[mb];
+#pragma unroll
+        for (int m = 0; m < L2; ++m)
+          if (m != mb) gm[m] = up ? gm[m] + Mmm[m][mb] : gm[m] - Mmm[m][mb];
+#pragma unroll
+        for (int j = 0; j < L1; ++j) q[j] = up ? q[j] + Mim[j][mb] : q[j] - Mim[j][mb];
+      }
+      const float mbk = inner_min_open_smem<L1>(A, q, ptab);
+      const unsigned id = obase | gray_c((unsigned)s);
+      g2 = fminf(g2, fmaxf(g1, mbk));
+      const bool better = mbk < g1;
+      g1 = better ? mbk : g1;
+      blk = better ? id : blk;
+    }
+    ev += (unsigned long long)nsteps * NI;
+  };
+  __syncwarp(tmask);  // the pair table is complete
+
+  // round one: every owning lane walks its lowest-bound pattern
+  const __half taken = __ushort_as_half((unsigned short)0x7e00);  // NaN: passes no cut
+  if (own) {
+    const int o = lt | (ibest << nlb);
+    lb[o] = taken;
+    walk(o);
+  }
+  float cut = g1, c2 = g2;
+  team_top2(tmask, T, cut, c2);
+  cut = c2;
+  const float slack = 2.0f * bound;
+
+  // the patterns still below the cut, collected (lane order, at most kBnbBuf
+  // per pass; a taken pattern's bound becomes NaN) and walked in rounds of
+  // T, the cut re-checked and tightened every round; passes repeat until no
+  // pattern is left below the cut
+  const unsigned nmask = nst >= 32 ? 0xffffffffu : ((1u << nst) - 1u);
+  for (;;) {
+    const float thr = cut + slack;
+    unsigned smask = 0u;
+#pragma unroll
+    for (int i = 0; i < (1 << kBnbItBits); ++i)
+      smask |= (__half2float(lb[(lt | (i << nlb)) & (kBnbStates - 1)]) <= thr) ? (1u << i) : 0u;
+    smask &= nmask;
+    const int cnt = __popc(smask);
+    int pre = cnt;  // inclusive prefix over the team's lanes
+    for (int off = 1; off < T; off <<= 1) {
+      const int y = __shfl_up_sync(tmask, pre, off, T);
+      if (lt >= off) pre += y;
+    }
+    const int total = min(__shfl_sync(tmask, pre, T - 1, T), kBnbBuf);
+    if (total == 0) break;
+    int at = pre - cnt;
+    for (unsigned mm = smask; mm && at < kBnbBuf; mm &= mm - 1u, ++at) {
+      const int o = lt | ((__ffs(mm) - 1) << nlb);
+      rbuf[at] = (unsigned short)o;
+      rlb[at] = __half2float(lb[o]);
+      lb[o] = taken;
+    }
+    __syncwarp(tmask);
+    for (int r0 = 0; r0 < total; r0 += T) {
+      const int e = r0 + lt;
+      if (e < total && rlb[e] <= cut + slack) walk(rbuf[e]);
+      float t1 = g1, t2 = g2;
+      team_top2(tmask, T, t1, t2);
+      cut = fminf(cut, t2);
+    }
+    __syncwarp(tmask);
+  }
+  evaluated += ev;
+  m1 = g1;
+  b1 = blk;
+  m2 = g2;
+}
+
 // Top-two merge of (m1, b1, m2) triples; FP32 ties go to the pattern whose
 // charge vector is lexicographically smaller (bit-reversed order).
 __device__ __forceinline__ void top2_merge(float& m1, unsigned& b1, float& m2,
@@ -607,8 +986,8 @@ __device__ __forceinline__ void top2_merge(float& m1, unsigned& b1, float& m2,
 // and each rounding adds at most 2^-24 S.  The gap threshold is twice that.
 // (The recheck shortlists by the same margin, and the parity tests check on
 // every comparable pixel that no mismatch escapes it.)
-__device__ __forceinline__ float near_tie_bound(float S, int k, int L2) {
-  return 2.0f * (float)((1 << L2) + 2 * k + 8) * 5.9604645e-8f * S;
+__device__ __forceinline__ float near_tie_bound(float S, int k, int L2, int extra = 0) {
+  return 2.0f * (float)((1 << L2) + 2 * k + 8 + extra) * 5.9604645e-8f * S;
 }
 
 }  // namespace qa

@@ -138,7 +138,11 @@ __global__ void k_model_update(ModelData* md, int n, int ng, const double* Cdd,
     k.bx_qp_scale = __double2float_rn(8.0 * md->cond * (n + 1) * 5.9604644775390625e-8);
     const double e1 = md->cond * (n + 1) * 5.9604644775390625e-8;
     k.bx_qp_scale2 = __double2float_rn(8.0 * e1 * e1);
-    k.pad2[0] = k.pad2[1] = k.pad2[2] = 0;
+    float qn = 0.f;  // from M itself (the other lanes' Mhi stores are not ordered yet)
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < i; ++j) qn += fminf(0.f, __double2float_rn(md->M[i * n + j]));
+    k.qneg = qn;
+    k.pad2[0] = k.pad2[1] = 0;
     k.model_bad = md->status != 0;
     k.pad = 0;
   }
