@@ -778,8 +778,11 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
   unsigned db;
   unsigned long long ev = 0;
   static_assert(kResolveThreads <= 256, "the walk's team is the block: at most 8 lane bits");
+  // (outer patterns whose lower bound is above the threshold plus the FP32
+  // margin hold no block within the threshold)
   search_lane<L1, L2, CLOSED, true>(sM, sv, tid, kResolveThreads, thr, blist, &bcnt,
-                                    kCap, d1, db, d2, ev);
+                                    kCap, d1, db, d2, ev, nullptr, nullptr, nullptr,
+                                    thr + 2.0f * rec->bound, S.cs.qneg);
   __syncthreads();
   const unsigned nb = bcnt;
   const bool fits = nb <= kCap;
@@ -1079,7 +1082,8 @@ __device__ inline void recheck_entry(const GsLaunch& L, const ArrayDesc& a, Rech
   float d1, d2;
   unsigned db;
   search_lane<L1, L2, CLOSED, true>(sM, sv, tid, kRecheckThreads, thr, blist,
-                                    &bcount, kBcap, d1, db, d2, ev);
+                                    &bcount, kBcap, d1, db, d2, ev, nullptr, nullptr, nullptr,
+                                    thr + 2.0f * sbound, a.md->k.qneg);
   __syncthreads();
   const unsigned nb = bcount;
   const bool overflowed = nb > kBcap;

@@ -193,6 +193,10 @@ __device__ __forceinline__ float state_from_scratch(const float* sM,
 // BLOCKS: return the lane's best block minimum with its block id and the
 // second-best block minimum, for a team-level finish (team_finish).
 // LANEBITS: log2 of the widest team the caller uses (T <= 2^LANEBITS).
+// lb_cut (COLLECT): an outer pattern whose lower bound A + sum min(0, q_j) +
+// sum min(0, g_m) + qneg (qneg: the model's bound of any pair-term sum, so
+// the bound holds for every candidate of the pattern) lies above lb_cut
+// holds no block to collect and is skipped.
 template <int L1, int L2, bool CLOSED, bool COLLECT, bool BLOCKS = false, int LANEBITS = 8>
 __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
                                             const SlotView sv, int t, int T,
@@ -202,7 +206,8 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
                                             unsigned long long& evaluated,
                                             const float* __restrict__ colt = nullptr,
                                             const float* __restrict__ itab = nullptr,
-                                            float* __restrict__ cslot = nullptr) {
+                                            float* __restrict__ cslot = nullptr,
+                                            float lb_cut = kInf, float qneg = 0.f) {
   static_assert(L1 >= 2 && L1 <= 6 && L2 >= 0 && L2 <= 5, "search split");
   // block-level searches with at least 9 inner + middle slots take the
   // iteration slots' terms from the team table itab (iter_build): at most 7
@@ -377,6 +382,14 @@ __device__ __forceinline__ void search_lane(const float* __restrict__ sM,
       for (int j = 0; j < L1; ++j) q[j] += Mrow[dI[j]];
 #pragma unroll
       for (int m = 0; m < L2; ++m) gm[m] += Mrow[dM[m]];
+    }
+    if (COLLECT) {
+      float sb = 0.f;
+#pragma unroll
+      for (int j = 0; j < L1; ++j) sb += fminf(0.f, q[j]);
+#pragma unroll
+      for (int m = 0; m < L2; ++m) sb += (m < nmid) ? fminf(0.f, gm[m]) : 0.f;
+      if ((A + sb) + qneg > lb_cut) continue;
     }
     const unsigned obase = o << L2;
     const int popo = __popc(o);
