@@ -326,9 +326,11 @@ qa::SearchCfg choose_cfg(int n, double t, long long P, int num_sms, bool closed)
   if (n <= 2) c = {2, 0, 1};
   else if (ke <= 4) c = {4, 0, 1};
   else if (ke <= 7) c = {4, 3, 1};
-  else if (!closed && ke >= 10) {
-    // open arrays with many ambiguous dots: the pruned search, 16-lane teams
-    // (two pixels per warp), 32 on rasters too small to fill the GPU
+  else if (ke >= 15) {
+    // nearly every dot ambiguous among 15 or 16: the pruned search, 16-lane
+    // teams (two pixels per warp), 32 on rasters too small to fill the GPU
+    // (below that the exhaustive search costs less than the pruned search's
+    // fixed per-pixel set-up: measured on 128 x 128 rasters of 10 to 16 dots)
     c = {qa::kBnbL1, qa::kBnbL2, qa::kBnbMinT};
     if (P * c.T < (long long)num_sms * 128 * 4) c.T = 32;
     return c;
@@ -1220,7 +1222,7 @@ int qa_batch_create(const qa_batch_item* items, int count, qa_batch** out) {
                        it.closed != 0);  // no small-raster spreading
     if (it.team) d.cfg.T = it.team;
     // the pruned search needs teams of kBnbMinT lanes or more
-    if (qa::bnb_search(d.cfg.L1, d.cfg.L2, it.closed != 0) && d.cfg.T < qa::kBnbMinT)
+    if (qa::bnb_search(d.cfg.L1, d.cfg.L2) && d.cfg.T < qa::kBnbMinT)
       d.cfg.T = qa::kBnbMinT;
     d.klass = qa::search_klass(d.cfg);
     d.prep_team = prep_team(m->n);

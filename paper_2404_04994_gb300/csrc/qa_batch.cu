@@ -86,10 +86,11 @@ __global__ void __launch_bounds__(kSearchThreads) k_search_batch(GsLaunch L, int
   search_batch_units<L1, L2, CLOSED, TF>(L, v);
 }
 
-// The pruned search's variant (open, 5 + 2 split, teams of kBnbMinT+ lanes),
+// The pruned search's variants (5 + 2 split, teams of kBnbMinT+ lanes),
 // built for kBnbBlocks resident blocks per SM.
+template <bool CLOSED>
 __global__ void __launch_bounds__(kSearchThreads, kBnbBlocks) k_search_batch_bnb(GsLaunch L, int v) {
-  search_batch_units<kBnbL1, kBnbL2, false, true>(L, v);
+  search_batch_units<kBnbL1, kBnbL2, CLOSED, true>(L, v);
 }
 
 // The kernel of variant v = 4 klass + 2 closed + team finish.
@@ -100,10 +101,10 @@ static BatchSearchKernel batch_search_kernel(int v) {
       k_search_batch<l1, l2, true, false>, k_search_batch<l1, l2, true, true>
   static const BatchSearchKernel table[kBatchVariants] = {
       QA_V(2, 0), QA_V(4, 0), QA_V(4, 3), QA_V(5, 4),
-      k_search_batch<5, 2, false, false>, k_search_batch_bnb,
-      k_search_batch<5, 2, true, false>, k_search_batch<5, 2, true, true>};
-  static_assert(bnb_search(kBnbL1, kBnbL2, false) && kBnbL1 == 5 && kBnbL2 == 2,
-                "variant 4 klass + 1 is the pruned search");
+      k_search_batch<5, 2, false, false>, k_search_batch_bnb<false>,
+      k_search_batch<5, 2, true, false>, k_search_batch_bnb<true>};
+  static_assert(bnb_search(kBnbL1, kBnbL2) && kBnbL1 == 5 && kBnbL2 == 2,
+                "the block-level variants of klass 4 are the pruned search");
 #undef QA_V
   return (v >= 0 && v < kBatchVariants) ? table[v] : nullptr;
 }
@@ -117,8 +118,8 @@ int batch_search_occupancy(int v) {
 }
 
 // Resident blocks per SM of the persistent prep kernel and of the search of
-// the large open arrays' variant (the pruned search, 5 + 2 split, team
-// finish), for unit sizing.
+// the large arrays' variant (the pruned search, 5 + 2 split, open), for unit
+// sizing.
 void batch_occupancy(int* prep_per_sm, int* search_per_sm) {
   *prep_per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(prep_per_sm, k_prep_batch, kPrepThreads, 0);

@@ -374,7 +374,7 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
     // the pruned search walks a shallower middle level than the resolve's
     // re-walk (kCheckL2), which shortlists by this bound, and forms each
     // rest state from up to kBnbItBits + 2 more table sums
-    rec->bound = bnb_search(a.cfg.L1, a.cfg.L2, CLOSED)
+    rec->bound = bnb_search(a.cfg.L1, a.cfg.L2)
                      ? near_tie_bound(S, k, max(a.cfg.L2, kCheckL2), kBnbItBits + 2)
                      : near_tie_bound(S, k, a.cfg.L2);
     my_cand = CLOSED ? binom(k, w) : (1ull << k);
@@ -472,9 +472,9 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
   const PixRec* rec = a.recs + (active ? p : 0);
   const unsigned mask = active ? rec->mask : 0u;
   const int k = __popc(mask);
-  // BNB: the pruned search (open, 5 + 2 split, teams of kBnbMinT+ lanes,
-  // which the host guarantees for this split)
-  constexpr bool BNB = TF && bnb_search(L1, L2, CLOSED);
+  // BNB: the pruned search (5 + 2 split, teams of kBnbMinT+ lanes, which
+  // the host guarantees for this split)
+  constexpr bool BNB = TF && bnb_search(L1, L2);
   int* sdot = BNB ? sh.u.bnb.sdot[team] : TF ? sh.u.team.sdot[team] : sh.u.lane.sdot[team];
   float* sht = BNB ? sh.u.bnb.sh[team] : TF ? sh.u.team.sh[team] : sh.u.lane.sh[team];
   int* slot_of = BNB ? sh.u.bnb.slot_of[team] : nullptr;
@@ -533,7 +533,7 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
       const unsigned wl = threadIdx.x & 31u;
       const unsigned tmask =
           T >= 32 ? kFull : (((1u << T) - 1u) << (wl & ~(unsigned)(T - 1)));
-      search_bnb(sM, sv, lt, T, tmask, rec->bound, sh.cs.qneg, sh.u.bnb.pm[team],
+      search_bnb<CLOSED>(sM, sv, lt, T, tmask, rec->bound, sh.cs.qneg, sh.u.bnb.pm[team],
                  sh.u.bnb.vv[team], sh.u.bnb.itab[team],
                  sh.u.bnb.ltab[team * T], sh.u.bnb.lb[team], sh.u.bnb.rbuf[team],
                  sh.u.bnb.rlb[team], sh.u.bnb.ptab[team], m1, b1, m2, ev);

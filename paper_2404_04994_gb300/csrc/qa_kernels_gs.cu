@@ -72,8 +72,9 @@ __global__ void __launch_bounds__(kSearchThreads) k_ground_state(GsLaunch L) {
 }
 
 // The pruned search's tiles, built for kBnbBlocks resident blocks per SM.
+template <bool CLOSED>
 __global__ void __launch_bounds__(kSearchThreads, kBnbBlocks) k_ground_state_bnb(GsLaunch L) {
-  ground_state_tile<kBnbL1, kBnbL2, false, true>(L);
+  ground_state_tile<kBnbL1, kBnbL2, CLOSED, true>(L);
 }
 
 // Search alone, behind k_prep (programmatic dependent launch): for tilings
@@ -106,8 +107,9 @@ __global__ void __launch_bounds__(kSearchThreads) k_search(GsLaunch L) {
   search_only_tile<L1, L2, CLOSED, TF>(L);
 }
 
+template <bool CLOSED>
 __global__ void __launch_bounds__(kSearchThreads, kBnbBlocks) k_search_bnb(GsLaunch L) {
-  search_only_tile<kBnbL1, kBnbL2, false, true>(L);
+  search_only_tile<kBnbL1, kBnbL2, CLOSED, true>(L);
 }
 
 // Near-tie list: one block per entry, grid-stride.  In a batched call the
@@ -231,14 +233,14 @@ static cudaError_t run(const GsLaunch& L, cudaStream_t st) {
   // on entry; resolve and recheck start early behind their predecessor
   cudaError_t e = cudaSuccess;
   if (L.ev) cudaEventRecord(L.ev[0], st);
-  // the pruned search (5 + 2 split, open; teams of kBnbMinT+ lanes) has
-  // kernels of its own, built for kBnbBlocks resident blocks per SM
-  constexpr bool kBnb = bnb_search(L1, L2, CLOSED);
+  // the pruned search (5 + 2 split; teams of kBnbMinT+ lanes) has kernels
+  // of its own, built for kBnbBlocks resident blocks per SM
+  constexpr bool kBnb = bnb_search(L1, L2);
   const bool tf = L.one.cfg.T >= kTeamFinishMin;
   if (fused_tiles(L)) {
     if (L.ev) cudaEventRecord(L.ev[1], st);
     if (kBnb && tf)
-      k_ground_state_bnb<<<search_blocks(L), kSearchThreads, 0, st>>>(L);
+      k_ground_state_bnb<CLOSED><<<search_blocks(L), kSearchThreads, 0, st>>>(L);
     else if (tf)
       k_ground_state<L1, L2, CLOSED, !kBnb><<<search_blocks(L), kSearchThreads, 0, st>>>(L);
     else
@@ -250,7 +252,7 @@ static cudaError_t run(const GsLaunch& L, cudaStream_t st) {
     if (L.ev) cudaEventRecord(L.ev[1], st);
     if (e == cudaSuccess) {
       if (kBnb && tf)
-        e = launch_dependent(k_search_bnb, (unsigned)search_blocks(L), kSearchThreads, st, L);
+        e = launch_dependent(k_search_bnb<CLOSED>, (unsigned)search_blocks(L), kSearchThreads, st, L);
       else if (tf)
         e = launch_dependent(k_search<L1, L2, CLOSED, !kBnb>, (unsigned)search_blocks(L),
                              kSearchThreads, st, L);

@@ -39,7 +39,7 @@ struct ArrayDesc {
 constexpr int kSearchThreads = 128;  // threads of a search block
 constexpr int kTeamFinishMin = 8;    // teams at least this wide finish the winning block together
 // The pruned search (branch and bound over the outer slots, qa_search.cuh):
-// open arrays with the 5 + 2 split, teams of kBnbMinT or 32 lanes.
+// arrays with the 5 + 2 split, teams of kBnbMinT or 32 lanes.
 constexpr int kBnbL1 = 5, kBnbL2 = 2;
 constexpr int kBnbMinT = 16;
 constexpr int kBnbBlocks = 5;  // resident blocks per SM its kernels are built for
@@ -47,8 +47,8 @@ constexpr int kBnbBlocks = 5;  // resident blocks per SM its kernels are built f
 constexpr int kBatchVariants = 20;
 static_assert(sizeof(((Counters*)nullptr)->q_var) / sizeof(unsigned) == kBatchVariants,
               "one queue head per batched search variant");
-__host__ __device__ constexpr bool bnb_search(int L1, int L2, bool closed) {
-  return !closed && L1 == kBnbL1 && L2 == kBnbL2;
+__host__ __device__ constexpr bool bnb_search(int L1, int L2) {
+  return L1 == kBnbL1 && L2 == kBnbL2;
 }
 
 // Pixels [first, first + count) of one array of a batched call.

@@ -109,6 +109,45 @@ __device__ __forceinline__ float inner_min_open_smem(float A, const float* q,
   return fminf(m0, m1);
 }
 
+// Closed, with the pair table P in shared memory: the minimum over the inner
+// patterns with popcount r (kInf if none).
+template <int L1>
+__device__ __forceinline__ float inner_min_closed_smem(float A, const float* q,
+                                                       const float* __restrict__ P, int r) {
+  constexpr int NI = 1 << L1;
+  float S[NI];
+  S[0] = A;
+  S[1] = __fadd_rn(A, q[0]);
+#pragma unroll
+  for (int j = 1; j < L1; ++j) {
+    const float2 qq = make_float2(q[j], q[j]);
+#pragma unroll
+    for (int b = 0; b < (1 << j); b += 2) {
+      const float2 e = fadd2(make_float2(S[b], S[b + 1]), qq);
+      S[b + (1 << j)] = e.x;
+      S[b + 1 + (1 << j)] = e.y;
+    }
+  }
+  float acc[L1 + 1];
+#pragma unroll
+  for (int i = 0; i <= L1; ++i) acc[i] = kInf;
+  const float4* P4 = reinterpret_cast<const float4*>(P);
+#pragma unroll
+  for (int b = 0; b < NI; b += 4) {
+    const float4 p = P4[b / 4];
+    const float2 e = fadd2(make_float2(S[b], S[b + 1]), make_float2(p.x, p.y));
+    const float2 f = fadd2(make_float2(S[b + 2], S[b + 3]), make_float2(p.z, p.w));
+    acc[popc_c(b)] = fminf(acc[popc_c(b)], e.x);
+    acc[popc_c(b + 1)] = fminf(acc[popc_c(b + 1)], e.y);
+    acc[popc_c(b + 2)] = fminf(acc[popc_c(b + 2)], f.x);
+    acc[popc_c(b + 3)] = fminf(acc[popc_c(b + 3)], f.y);
+  }
+  float res = kInf;
+#pragma unroll
+  for (int i = 0; i <= L1; ++i) res = (i == r) ? acc[i] : res;
+  return res;
+}
+
 // Closed: minimum over the inner patterns with popcount r (kInf if none).
 template <int L1>
 __device__ __forceinline__ float inner_min_closed(float A, const float* q,
@@ -644,8 +683,8 @@ __device__ __forceinline__ void team_finish(const float* __restrict__ sM, const 
 }
 
 // ---------------------------------------------------------------------------
-// Pruned search: open arrays, teams of 16 or 32 lanes, split L1 = 5, L2 = 2.
-// An exact branch and bound over the outer slots.
+// Pruned search: teams of 16 or 32 lanes, split L1 = 5, L2 = 2.  An exact
+// branch and bound over the outer slots.
 //
 // With the inner and middle slots x (L1 + L2 of them) free and the outer
 // pattern o fixed, a candidate's energy is
@@ -655,7 +694,10 @@ __device__ __forceinline__ void team_finish(const float* __restrict__ sM, const 
 // sum of the model's negative pair terms (0 whenever M is entrywise
 // non-negative, as for every Maxwell Cdd, whose inverse is non-negative), so
 //     LB_o = A_o + sum_j min(0, L_oj) + qneg
-// bounds every candidate of o from below.  An outer pattern whose bound lies
+// bounds every candidate of o from below.  A closed array's candidates of o
+// set exactly r = w - |o| walked slots (w the candidate weight of Sec. III.B's
+// closed filter), so there the bound is A_o + (the sum of the r smallest
+// L_oj) + qneg, and +inf when no such candidate exists.  An outer pattern whose bound lies
 // above an energy already known to be at least the runner-up (plus the FP32
 // error margin) holds neither the argmin nor the runner-up: it is skipped,
 // and the top two over the candidate set are exactly those over the patterns
@@ -750,6 +792,21 @@ __device__ __forceinline__ void team_top2(unsigned tmask, int T, float& a1, floa
   }
 }
 
+// Ascending sort of seven values (a 16-comparator network).
+__device__ __forceinline__ void bnb_sort7(float* c) {
+  auto cx = [&](int a, int b) {
+    const float lo = fminf(c[a], c[b]), hi = fmaxf(c[a], c[b]);
+    c[a] = lo;
+    c[b] = hi;
+  };
+  cx(0, 6); cx(2, 3); cx(4, 5);
+  cx(0, 2); cx(1, 4); cx(3, 6);
+  cx(0, 1); cx(2, 5); cx(3, 4);
+  cx(1, 2); cx(4, 6);
+  cx(2, 3); cx(4, 5);
+  cx(1, 2); cx(3, 4); cx(5, 6);
+}
+
 // Rest state of outer pattern o from the team tables: the lane part of its
 // lane bits, the iteration part of its iteration bits, and their pair terms.
 __device__ __forceinline__ void bnb_rest(const float* ltab, const float* itab, int nlb, int o,
@@ -783,6 +840,7 @@ __device__ __forceinline__ void bnb_rest(const float* ltab, const float* itab, i
 // single-flip energies, (1 << kBnbItBits) kBnbStride-rows, a kBnbLane-row per
 // lane, kBnbStates FP16 bounds, kBnbBuf collected patterns and their bounds,
 // 2^L1 inner pair terms, 16-byte aligned).
+template <bool CLOSED>
 __device__ __forceinline__ void search_bnb(const float* __restrict__ sM, const SlotView sv,
                                            int lt, int T, unsigned tmask, float bound,
                                            float qneg, float* pm, float* vv, float* itab,
@@ -800,6 +858,8 @@ __device__ __forceinline__ void search_bnb(const float* __restrict__ sM, const S
   const int nit = nout - nlb;
   const int nsteps = 1 << nmid;
   const bool own = lt < (1 << nlb);
+  const int w = sv.w;                                   // closed: candidate weight
+  const int lpop = __popc((unsigned)lt & ((1u << nlb) - 1u));  // the lane bits set
 
   // team tables: slot pairs and single-flip energies first, then the
   // iteration slots' terms and each owning lane's lane-bit part with its pair
@@ -854,11 +914,27 @@ __device__ __forceinline__ void search_bnb(const float* __restrict__ sM, const S
     for (int ii = 0; ii < kBnbItBits; ++ii)
       if ((i >> ii) & 1) x += cr[ii];
     const float A = (At + x) + i0.x;
-    const float s0 = fminf(0.f, Lt[0] + i0.y) + fminf(0.f, Lt[1] + i0.z);
-    const float s1 = fminf(0.f, Lt[2] + i0.w) + fminf(0.f, Lt[3] + i1.x);
-    const float s2 = fminf(0.f, Lt[4] + i1.y) + fminf(0.f, Lt[5] + i1.z);
-    const float s3 = fminf(0.f, Lt[6] + i1.w);
-    const float v = (A + ((s0 + s1) + (s2 + s3))) + qneg;
+    float v;
+    if (!CLOSED) {
+      const float s0 = fminf(0.f, Lt[0] + i0.y) + fminf(0.f, Lt[1] + i0.z);
+      const float s1 = fminf(0.f, Lt[2] + i0.w) + fminf(0.f, Lt[3] + i1.x);
+      const float s2 = fminf(0.f, Lt[4] + i1.y) + fminf(0.f, Lt[5] + i1.z);
+      const float s3 = fminf(0.f, Lt[6] + i1.w);
+      v = (A + ((s0 + s1) + (s2 + s3))) + qneg;
+    } else {
+      // the r smallest coefficients of the live walked slots (a sorting
+      // network on seven values; absent slots sort last)
+      float c[kBnbIn] = {Lt[0] + i0.y, Lt[1] + i0.z, Lt[2] + i0.w, Lt[3] + i1.x,
+                         Lt[4] + i1.y, Lt[5] + i1.z, Lt[6] + i1.w};
+#pragma unroll
+      for (int j = 0; j < kBnbIn; ++j) c[j] = j < k ? c[j] : kBig;
+      bnb_sort7(c);
+      const int r = w - (lpop + popc_c((unsigned)i));
+      float sr = 0.f;
+#pragma unroll
+      for (int j = 0; j < kBnbIn; ++j) sr = fmaf(j < r ? 1.f : 0.f, c[j], sr);
+      v = (r < 0 || r > min(k, kBnbIn)) ? kInf : (A + sr) + qneg;
+    }
     // stored rounded down to FP16: still a lower bound, half the space
     if (i < nst) lb[lt | (i << nlb)] = __float2half_rd(v);
     const bool better = i < nst && v < lbest;
@@ -915,7 +991,13 @@ __device__ __forceinline__ void search_bnb(const float* __restrict__ sM, const S
 #pragma unroll
         for (int j = 0; j < L1; ++j) q[j] = up ? q[j] + Mim[j][mb] : q[j] - Mim[j][mb];
       }
-      const float mbk = inner_min_open_smem<L1>(A, q, ptab);
+      float mbk;
+      if (!CLOSED) {
+        mbk = inner_min_open_smem<L1>(A, q, ptab);
+      } else {
+        const int rr = w - __popc((unsigned)o) - popc_c(gray_c((unsigned)s));
+        mbk = inner_min_closed_smem<L1>(A, q, ptab, rr);
+      }
       const unsigned id = obase | gray_c((unsigned)s);
       g2 = fminf(g2, fmaxf(g1, mbk));
       const bool better = mbk < g1;
