@@ -246,17 +246,31 @@ def run_ours(args):
     # one comparison, plus the middle Gray step (L1 + L2 adds and a 3-op top-two
     # update) shared by the 2^L1 slots of a block
     ops_per_slot = 3.0 + (L1 + L2 + 3.0) / (1 << L1)
-    ops = st["evaluated"] * ops_per_slot
+    # the pruned search (5 + 2 split) also bounds every outer pattern of every
+    # pixel: 2^(k - 7) patterns (k = 16 ambiguous dots at t = 1), each bound
+    # A + sum_j min(0, L_j) costing about 25 FP32 lane-operations (the lane's
+    # iteration-slot pair terms ~2.5, A 2, the seven L_j 7, their minima with
+    # 0 7, the sum 6, the pair-term floor 1)
+    pruned = (L1, L2) == (5, 2)
+    ops_per_bound = 25.0
+    bounds = P * (1 << max(n_dot - L1 - L2, 0)) if pruned else 0
+    ops = st["evaluated"] * ops_per_slot + bounds * ops_per_bound
     ms_s = statistics.mean(search_ms)
     achieved = ops / (ms_s * 1e-3) / 1e12
     sm_max = (clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = n_sm * 128 * sm_max * 1e6 / 1e12   # FP32 lanes x clock
+    # the same diagram searched exhaustively by the split walk (every one of
+    # the 2^16 candidates at 3.375 lane-operations): what the pruning saves
+    exh = st["candidates"] * 3.375 / (ms_s * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3),
                 "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": search_traffic(),
-                "kernel": "k_ground_state<5,4,open> (prep + search of each tile)",
+                "kernel": ("k_ground_state_bnb<open> (prep + pruned search of each tile)"
+                           if pruned else f"k_ground_state<{L1},{L2},open> (prep + search)"),
                 "ops_per_launch": ops,
                 "ops_per_evaluated_slot": ops_per_slot,
+                "bounds_per_launch": bounds, "ops_per_bound": ops_per_bound,
+                "exhaustive_equivalent_tops": round(exh, 3),
                 # k_ground_state runs the prep and the search of each tile, so
                 # its time covers both; the separate prep kernel does not run
                 "kernel_ms": round(ms_s, 5),
