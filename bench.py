@@ -432,10 +432,14 @@ def extra_measurements(api, torch, flush, args):
         from paper_2404_04994_gb300 import autograd as qag
         for kT in (0.01, 0.05):
             c = inputs.grid8(kT=kT)
+            # the fused library step (graph replay and plain launches), and
+            # the same step through torch autograd + torch.optim.Adam
             ms_step = qag.time_grad_step(c, kT, flush=flush)
             out[f"grad_step_ms_grid8_kT{kT:g}"] = ms_step
             out[f"grad_step_plain_ms_grid8_kT{kT:g}"] = qag.time_grad_step(c, kT, flush=flush,
                                                                          graph=False)
+            out[f"grad_step_autograd_ms_grid8_kT{kT:g}"] = qag.time_grad_step(
+                c, kT, flush=flush, fused=False)
     except ImportError:
         pass
     return out

@@ -144,8 +144,9 @@ int qa_model_update(qa_model* m, const double* Cdd, const double* Cgd);
 int qa_model_update_async(qa_model* m, const double* Cdd, const double* Cgd, void* stream);
 
 /* Replace the capacitances from DEVICE FP64 Maxwell matrices (same shape) and
- * recompute M = Cdd^-1 by an FP64 Cholesky on the GPU, asynchronously on
- * `stream`.  A Cholesky failure is recorded on the device; the next call that
+ * recompute M = Cdd^-1 on the GPU in FP64 (symmetric sweeps, i.e. Gauss-Jordan
+ * on diagonal pivots), asynchronously on `stream`.  A non-positive pivot (Cdd
+ * not positive definite) is recorded on the device; the next call that
  * reads the model on that stream writes QA_FLAG_UNRESOLVED for every pixel and
  * qa_model_stats reports it (host checks are impossible without a sync).
  * Used by the capacitance-fitting loop. */
@@ -321,6 +322,36 @@ int qa_soft_occupation_backward_ctx(qa_model* m, const qa_raster* r, double kT,
                                     const float* grad_mean, const float* mean,
                                     const void* ctx, double* dL_dCdd, double* dL_dCgd,
                                     void* stream);
+
+/* Adam hyper-parameters (Kingma & Ba, arXiv 1412.6980, Algorithm 1). */
+typedef struct {
+    double lr;      /* step size, > 0                  */
+    double beta1;   /* first-moment decay, [0, 1)      */
+    double beta2;   /* second-moment decay, [0, 1)     */
+    double eps;     /* denominator offset, > 0         */
+} qa_adam;
+
+/* One capacitance-fitting step on the GPU, fused: the capacitances Cdd, Cgd
+ * (DEVICE FP64, [n_dot x n_dot] and [n_dot x n_gate], the parameters) go into
+ * the model (FP64 Cholesky on the GPU, as qa_model_update_dev), the soft
+ * occupation <n> of Eq. "softargmin" is formed on the raster, the mean squared
+ * error against `target` and its gradient dL/d<n> are formed per pixel inside
+ * the same kernel, the gradient goes back to (Cdd, Cgd) as in
+ * qa_soft_occupation_backward, and one Adam step updates Cdd and Cgd in place.
+ *   per_dot = 0: target DEVICE FP32 [H, W], L = mean_p (sum_i <n_i> - target_p)^2
+ *   per_dot = 1: target DEVICE FP32 [H, W, n_dot], L = mean_{p,i} (<n_i> - target_pi)^2
+ * opt_state: DEVICE FP64 [2 (n_dot^2 + n_dot n_gate) + 1], caller-owned and
+ * zeroed before the first step (first moments, second moments, step count).
+ * loss (DEVICE FP32 scalar), dL_dCdd, dL_dCgd (DEVICE FP64) and out_mean
+ * (DEVICE FP32 [H, W, n_dot]) are optional outputs (NULL to skip), all taken
+ * at the parameters before the update.  Everything is enqueued on `stream`
+ * with no host synchronisation, so a warmed-up step can be captured in a CUDA
+ * graph.  Cdd must stay positive definite; a non-positive pivot is handled as in
+ * qa_model_update_dev. */
+int qa_fit_step(qa_model* m, const qa_raster* r, double kT, double threshold, int closed,
+                int n_charges, const float* target, int per_dot, double* Cdd, double* Cgd,
+                double* opt_state, const qa_adam* opt, float* loss, double* dL_dCdd,
+                double* dL_dCgd, float* out_mean, void* stream);
 
 /* Record CUDA events around each kernel that later calls on this model
  * enqueue (enable = 1) or stop doing so (0, the default).  The device time of

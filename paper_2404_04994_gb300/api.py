@@ -71,6 +71,11 @@ class qa_sensor_params(ctypes.Structure):
                 ("jump_prob", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
 
 
+class qa_adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("beta2", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
 QA_SENSOR_LORENTZIAN = 0
 QA_SENSOR_GAUSSIAN = 1
 
@@ -135,6 +140,8 @@ def load():
         "qa_soft_occupation_backward_ctx": (I, [P, ctypes.POINTER(qa_raster),
                                                 ctypes.c_double, ctypes.c_double, I, I,
                                                 P, P, P, P, P, P]),
+        "qa_fit_step": (I, [P, ctypes.POINTER(qa_raster), ctypes.c_double, ctypes.c_double,
+                            I, I, P, I, P, P, P, ctypes.POINTER(qa_adam), P, P, P, P, P]),
         "qa_model_stats": (I, [P, P, ctypes.POINTER(qa_stats)]),
         "qa_model_set_timing": (I, [P, I]),
         "qa_ground_state_open_static": (I, [P, ctypes.POINTER(qa_raster),
@@ -483,6 +490,32 @@ def qa_soft_occupation_backward_ctx(m, raster, kT, threshold, closed, n_charges,
         _dev(mean, torch.float32, P * n, "mean"), _dev(ctx, torch.int64, P, "ctx"),
         _dev(dL_dCdd, torch.float64, n * n, "dL_dCdd"),
         _dev(dL_dCgd, torch.float64, n * ng, "dL_dCgd"), _stream(stream)))
+
+
+def fit_state_len(n, ng):
+    """Doubles of qa_fit_step's optimiser state: first and second moments of
+    every parameter, then the step count."""
+    return 2 * (n * n + n * ng) + 1
+
+
+def qa_fit_step(m, raster, kT, threshold, closed, n_charges, target, per_dot, Cdd, Cgd,
+                opt_state, lr, beta1=0.9, beta2=0.999, eps=1e-8, loss=None, dL_dCdd=None,
+                dL_dCgd=None, out_mean=None, stream=None):
+    """One fused fitting step: model update, soft occupation, MSE against
+    target, gradient and an Adam step on Cdd, Cgd (in place)."""
+    import torch
+    n, ng = qa_model_shape(m)
+    r = make_raster(raster, ng)
+    P = r.W * r.H
+    opt = qa_adam(float(lr), float(beta1), float(beta2), float(eps))
+    _check(load().qa_fit_step(
+        m, ctypes.byref(r), float(kT), float(threshold), int(closed), int(n_charges),
+        _dev(target, torch.float32, P * n if per_dot else P, "target"), int(bool(per_dot)),
+        _dev(Cdd, torch.float64, n * n, "Cdd"), _dev(Cgd, torch.float64, n * ng, "Cgd"),
+        _dev(opt_state, torch.float64, fit_state_len(n, ng), "opt_state"), ctypes.byref(opt),
+        _dev(loss, torch.float32, 1, "loss"), _dev(dL_dCdd, torch.float64, n * n, "dL_dCdd"),
+        _dev(dL_dCgd, torch.float64, n * ng, "dL_dCgd"),
+        _dev(out_mean, torch.float32, P * n, "out_mean"), _stream(stream)))
 
 
 def qa_model_set_timing(m, enable=True):

@@ -542,12 +542,23 @@ int run_ground_state(qa_model* m, const ScanIn& in, double t, int closed,
   return QA_OK;
 }
 
+// the fit step's extra arguments (qa_fit_step)
+struct FitArgs {
+  const float* target;
+  int per_dot;
+  float* loss;
+  double* Cdd;
+  double* Cgd;
+  double* state;
+  qa_adam opt;
+};
+
 int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
              int n_charges, float* out_mean, float* out_logZ,
              const float* grad_mean, double* dCdd, double* dCgd, void* stream,
              uint2* ctx_out = nullptr, const uint2* ctx_in = nullptr,
-             const float* mean_in = nullptr) {
-  const bool bwd = grad_mean != nullptr;
+             const float* mean_in = nullptr, const FitArgs* fit = nullptr) {
+  const bool bwd = grad_mean != nullptr || fit != nullptr;
   if (!m) return fail(QA_ERR_INVALID, "null model");
   if (!r) return fail(QA_ERR_INVALID, "null raster");
   if (!(kT > 0.0) || !std::isfinite(kT)) return fail(QA_ERR_RANGE, "kT=%g must be > 0", kT);
@@ -555,7 +566,7 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
   if (closed && (n_charges < 0 || n_charges > 100000))
     return fail(QA_ERR_RANGE, "n_charges=%d out of range", n_charges);
   if (!bwd && !out_mean) return fail(QA_ERR_INVALID, "null out_mean");
-  if (bwd && (!dCdd || !dCgd)) return fail(QA_ERR_INVALID, "null gradient output");
+  if (bwd && !fit && (!dCdd || !dCgd)) return fail(QA_ERR_INVALID, "null gradient output");
   ScanIn in;
   in.r = r;
   qa::Scan sc;
@@ -643,6 +654,21 @@ int run_soft(qa_model* m, const qa_raster* r, double kT, double t, int closed,
   a.dL_dCdd = dCdd;
   a.dL_dCgd = dCgd;
   a.num_sms = m->num_sms;
+  if (fit) {
+    const double terms = (double)P * (fit->per_dot ? m->n : 1);
+    a.fit_target = fit->target;
+    a.fit_per_dot = fit->per_dot ? 1 : 0;
+    a.fit_scale = (float)(2.0 / terms);
+    a.fit_inv_count = 1.0 / terms;
+    a.loss_out = fit->loss;
+    a.fit_Cdd = fit->Cdd;
+    a.fit_Cgd = fit->Cgd;
+    a.fit_state = fit->state;
+    a.lr = fit->opt.lr;
+    a.beta1 = fit->opt.beta1;
+    a.beta2 = fit->opt.beta2;
+    a.eps = fit->opt.eps;
+  }
   m->last_cfg = cfg;
   m->last_P = P;
   a.ev = m->timing ? m->ev + 4 : nullptr;
@@ -976,6 +1002,30 @@ int qa_soft_occupation_backward_ctx(qa_model* m, const qa_raster* r, double kT,
   if (!grad_mean || !mean || !ctx) return fail(QA_ERR_INVALID, "null grad_mean, mean or ctx");
   return run_soft(m, r, kT, threshold, closed, n_charges, nullptr, nullptr, grad_mean,
                   dL_dCdd, dL_dCgd, stream, nullptr, (const uint2*)ctx, mean);
+}
+
+int qa_fit_step(qa_model* m, const qa_raster* r, double kT, double threshold, int closed,
+                int n_charges, const float* target, int per_dot, double* Cdd, double* Cgd,
+                double* opt_state, const qa_adam* opt, float* loss, double* dL_dCdd,
+                double* dL_dCgd, float* out_mean, void* stream) {
+  if (!m || !r || !target || !Cdd || !Cgd || !opt_state || !opt)
+    return fail(QA_ERR_INVALID, "null argument");
+  if (!(opt->lr > 0.0) || !std::isfinite(opt->lr))
+    return fail(QA_ERR_RANGE, "Adam lr=%g must be > 0", opt->lr);
+  if (!(opt->beta1 >= 0.0 && opt->beta1 < 1.0) || !(opt->beta2 >= 0.0 && opt->beta2 < 1.0))
+    return fail(QA_ERR_RANGE, "Adam betas (%g, %g) outside [0, 1)", opt->beta1, opt->beta2);
+  if (!(opt->eps > 0.0) || !std::isfinite(opt->eps))
+    return fail(QA_ERR_RANGE, "Adam eps=%g must be > 0", opt->eps);
+  if (!(kT > 0.0) || !std::isfinite(kT)) return fail(QA_ERR_RANGE, "kT=%g must be > 0", kT);
+  int rc = select_device(m);
+  if (rc) return rc;
+  cudaError_t e = qa::launch_model_update(m->d_md, m->n, m->ng, Cdd, Cgd, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "model update launch");
+  m->host_stale = true;
+  ++m->gen;
+  FitArgs f{target, per_dot ? 1 : 0, loss, Cdd, Cgd, opt_state, *opt};
+  return run_soft(m, r, kT, threshold, closed, n_charges, out_mean, nullptr, nullptr, dL_dCdd,
+                  dL_dCgd, stream, nullptr, nullptr, nullptr, &f);
 }
 
 int qa_model_stats(qa_model* m, void* stream, qa_stats* out) {

@@ -93,7 +93,7 @@ struct __align__(16) PixRec {
 };
 
 // FP32 / double-float constants of a model, derived once from the FP64
-// matrices whenever they change (host set-up or the device Cholesky) and
+// matrices whenever they change (host set-up or the device inverse) and
 // staged by every block with plain 16-byte loads.
 struct __align__(16) ModelConsts {
   float Mhi[kMaxDot * kLdM];   // M = Cdd^-1 as double-float (hi, lo)
@@ -103,7 +103,7 @@ struct __align__(16) ModelConsts {
   df vs[kMaxDot];              // Cdd 1 / (1^T Cdd 1)   (Appendix D)
   float s_s;                   // 1^T Cdd 1
   float bx_qp_scale;           // QP decision margin per unit of (1+|c|+N_hat)
-  int model_bad;               // device Cholesky of an updated Cdd failed
+  int model_bad;               // device inverse of an updated Cdd failed (not PD)
   int pad;
   float CddLo[kMaxDot * kLdM]; // Cdd - hi part (Cdd as double-float with Cdd above)
   df sv2[kMaxDot];             // Cdd 1 as double-float
@@ -113,7 +113,7 @@ struct __align__(16) ModelConsts {
   int pad2[2];
 };
 
-// Device copy of a model (written by the host or by the Cholesky kernel).
+// Device copy of a model (written by the host or by the device update).
 struct __align__(16) ModelData {
   double Cdd[kMaxDot * kMaxDot];
   double M[kMaxDot * kMaxDot];        // Cdd^-1

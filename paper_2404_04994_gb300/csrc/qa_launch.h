@@ -154,13 +154,25 @@ struct SoftLaunch {
   double* dL_dCgd;
   int num_sms;
   cudaEvent_t* ev;     // optional: events around the soft kernel(s)
+  // fit step: the kernel forms the MSE gradient of each pixel from its own
+  // <n> (no grad_mean input), the last stage adds up the loss and applies
+  // one Adam step to the parameters in place
+  const float* fit_target;  // [P] (target of sum_i <n_i>) or [P, n] (per dot); null otherwise
+  int fit_per_dot;
+  float fit_scale;          // 2 / (number of loss terms)
+  double fit_inv_count;     // 1 / (number of loss terms)
+  float* loss_out;          // device float, may be null
+  double* fit_Cdd;          // [n * n] parameters
+  double* fit_Cgd;          // [n * ng]
+  double* fit_state;        // [2 (n n + n ng) + 1]: first moments, second moments, step
+  double lr, beta1, beta2, eps;
 };
 
 cudaError_t launch_soft_forward(const SoftLaunch& a, cudaStream_t st);
 cudaError_t launch_soft_backward(const SoftLaunch& a, cudaStream_t st);
 size_t soft_partials_floats(int n, long long P, const SearchCfg& cfg);
 
-// FP64 Cholesky inverse of a device Cdd into the model (update_dev).
+// FP64 inverse (symmetric sweeps) of a device Cdd into the model (update_dev).
 cudaError_t launch_model_update(ModelData* md, int n, int ng,
                                 const double* Cdd_dev, const double* Cgd_dev,
                                 cudaStream_t st);

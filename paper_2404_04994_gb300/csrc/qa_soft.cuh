@@ -1,6 +1,6 @@
 // qa_soft.cuh -- finite-temperature occupation (Sec. IV.B, Eq.
 // "softargmin") over the method's candidate set, its gradient with the set
-// frozen, and the device FP64 Cholesky inverse used when the capacitances are
+// frozen, and the device FP64 inverse used when the capacitances are
 // updated on the GPU.
 //
 // Accuracy: at kT = 0.01 an energy error dU moves <n> by up to dU / (4 kT),
@@ -21,9 +21,10 @@ constexpr int kSoftThreads = 128;
 
 __host__ __device__ constexpr int tri(int n) { return n * (n + 1) / 2; }
 
-// length of one pixel's gradient contribution: upper triangle of dL/dM plus
-// three N-vectors (sum dc, sum ix dc, sum iy dc)
-__host__ __device__ inline int contrib_len(int n) { return tri(n) + 3 * n; }
+// length of one pixel's gradient contribution: upper triangle of dL/dM,
+// three N-vectors (sum dc, sum ix dc, sum iy dc) and, last, the pixel's loss
+// term of a fit step (0 otherwise)
+__host__ __device__ inline int contrib_len(int n) { return tri(n) + 3 * n + 1; }
 
 struct TeamSlots {
   int dot[kMaxDot];
@@ -59,6 +60,44 @@ __device__ __forceinline__ float delta_energy(const TeamSlots& ts, const float* 
     }
   }
   return D;
+}
+
+// Fit step, lane 0 of a team: the pixel's <n> from the slot weight sums
+// accb (slot order) and Z, then the MSE gradient g = dL/d<n> into gsh[0, n)
+// and the pixel's squared residual into lossp.  Sum target: residual r =
+// sum_i <n_i> - target_p and g_i = scale r for every dot; per-dot target:
+// r_i = <n_i> - target_pi and g_i = scale r_i.
+template <int K>
+__device__ __forceinline__ void fit_loss_grad(const SoftLaunch& a, const TeamSlots& ts,
+                                              const float* accb, float Z, long long p,
+                                              float* gsh, float& lossp) {
+  const int n = a.n;
+  float pred = 0.f;
+  for (int i = 0; i < n; ++i) {
+    float v = (float)ts.base[i];
+    if ((ts.mask >> i) & 1u) {
+      const int s = __popc(ts.mask & ((1u << i) - 1u));
+#pragma unroll
+      for (int q = 0; q < K; ++q)
+        if (q == s) v += accb[q] / Z;
+    }
+    gsh[i] = v;
+    if (a.out_mean) a.out_mean[p * n + i] = v;
+    pred += v;
+  }
+  float l = 0.f;
+  if (a.fit_per_dot) {
+    for (int i = 0; i < n; ++i) {
+      const float r = gsh[i] - a.fit_target[p * n + i];
+      l = fmaf(r, r, l);
+      gsh[i] = a.fit_scale * r;
+    }
+  } else {
+    const float r = pred - a.fit_target[p];
+    l = r * r;
+    for (int i = 0; i < n; ++i) gsh[i] = a.fit_scale * r;
+  }
+  lossp = l;
 }
 
 // Lane 0 of a team: pixel p's record into the team's slots (slot order: the
@@ -179,7 +218,7 @@ __device__ inline void soft_anchor(const SoftLaunch& a, TeamSlots& ts, const flo
 template <int KMAX>
 __device__ inline void soft_contrib(const SoftLaunch& a, TeamSlots& ts, const float* q_s,
                                     float* my, const float* s_contrib, const float* sM, int T,
-                                    int lt, int teams, bool active, long long p) {
+                                    int lt, int teams, bool active, long long p, float lossp) {
   const int n = a.n;
   const int L = contrib_len(n);
   const unsigned tmask = active ? ts.mask : 0u;
@@ -225,6 +264,7 @@ __device__ inline void soft_contrib(const SoftLaunch& a, TeamSlots& ts, const fl
     my[tri(n) + n + i] = dc * (float)ix;
     my[tri(n) + 2 * n + i] = dc * (float)iy;
   }
+  if (lt == 0) my[L - 1] = active ? lossp : 0.f;
   __syncthreads();
   // block sum over teams in fixed order (double-float), one partial per block
   float* out = a.partials + (size_t)blockIdx.x * 2 * L;
@@ -245,6 +285,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
   constexpr int kMaxTeams = kSoftThreads / (KMAX > 8 ? 32 : 4);
   __shared__ float slotM[kMaxTeams][KMAX * KMAX];
   __shared__ float sQa[BWD ? kMaxTeams : 1][tri(KMAX) + KMAX + 1];  // Qa, va, sa of a team
+  __shared__ float sGf[BWD ? kMaxTeams : 1][kMaxDot];                 // fit step: g of a team
   extern __shared__ float s_contrib[];  // BWD: [teams][contrib_len]
   const int n = a.n;
   stage_consts(&a.md->k, &cs);
@@ -345,20 +386,29 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
   const float invZ = 1.0f / Z;
 #pragma unroll
   for (int s = 0; s < KMAX; ++s) gs[s] = 0.f;
+  const bool fit = a.fit_target != nullptr;
+  float lossp = 0.f;
+  if (fit) {
+    if (active && lt == 0) fit_loss_grad<KMAX>(a, ts, acc, Z, p, sGf[team], lossp);
+    __syncwarp();
+  }
   if (active) {
-    const float* g = a.grad_mean + p * n;
+    const float* g = fit ? sGf[team] : a.grad_mean + p * n;
     for (int i = 0; i < n; ++i) gbase += g[i] * (float)ts.base[i];
-    if (use_ctx) {
-      for (int i = 0; i < n; ++i) gmean += g[i] * a.mean_in[p * n + i];
-    } else {
-      gmean = gbase;
-#pragma unroll
-      for (int s = 0; s < KMAX; ++s)
-        if (s < k) gmean += g[ts.dot[s]] * acc[s] * invZ;
-    }
 #pragma unroll
     for (int s = 0; s < KMAX; ++s)
       if (s < k) gs[s] = g[ts.dot[s]];
+    if (use_ctx) {
+      for (int i = 0; i < n; ++i) gmean += g[i] * a.mean_in[p * n + i];
+    } else {
+      // g . <n> - g . base = sum_s g_s <b_s>, so that gn - gmean below is
+      // formed without the large g . base on both sides
+      gmean = 0.f;
+#pragma unroll
+      for (int s = 0; s < KMAX; ++s)
+        if (s < k) gmean += gs[s] * acc[s] * invZ;
+      gbase = 0.f;
+    }
   }
   float sa = 0.f;
   float va[KMAX];
@@ -407,7 +457,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
     q_s[tri(KMAX) + KMAX] = sa;
   }
   __syncwarp();
-  soft_contrib<KMAX>(a, ts, q_s, my, s_contrib, sM, T, lt, teams, active, p);
+  soft_contrib<KMAX>(a, ts, q_s, my, s_contrib, sM, T, lt, teams, active, p, lossp);
 }
 
 // ---------------------------------------------------------------------------
@@ -501,6 +551,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
   __shared__ float slotM[kTeams][K * K];
   __shared__ float sQa[BWD ? kTeams : 1][tri(K) + K + 1];  // Qa, va, sa of a team
   __shared__ float sQd[BWD ? kTeams : 1][1 + K + tri(K - 1)];  // the same in flip coordinates
+  __shared__ float sGf[BWD ? kTeams : 1][kMaxDot];             // fit step: g of a team
   extern __shared__ float s_contrib[];                     // BWD: [teams][contrib_len]
   const int n = a.n;
   stage_consts(&a.md->k, &cs);
@@ -633,28 +684,38 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
   float gbase = 0.f, gmean = 0.f;
 #pragma unroll
   for (int s = 0; s < K; ++s) gs[s] = 0.f;
+  const bool fit = a.fit_target != nullptr;
+  float lossp = 0.f;
+  if (fit) {
+    if (active && lt == 0) fit_loss_grad<K>(a, ts, accb, Z, p, sGf[team], lossp);
+    __syncwarp();
+  }
   if (active) {
-    const float* g = a.grad_mean + p * n;
-    for (int i = 0; i < n; ++i) gbase += g[i] * (float)ts.base[i];
-    if (use_ctx) {
-      for (int i = 0; i < n; ++i) gmean += g[i] * a.mean_in[p * n + i];
-    } else {
-      gmean = gbase;
-#pragma unroll
-      for (int s = 0; s < K; ++s)
-        if (s < k) gmean += g[ts.dot[s]] * accb[s] / Z;
-    }
+    const float* g = fit ? sGf[team] : a.grad_mean + p * n;
 #pragma unroll
     for (int s = 0; s < K; ++s)
       if (s < k) gs[s] = g[ts.dot[s]];
+    if (use_ctx) {
+      for (int i = 0; i < n; ++i) gbase += g[i] * (float)ts.base[i];
+      for (int i = 0; i < n; ++i) gmean += g[i] * a.mean_in[p * n + i];
+    }
   }
-  // g . n* - g . <n> and the flip-coordinate gradient gam_s = sg_s g_s
-  float c0 = gbase - gmean;
+  // the flip-coordinate gradient gam_s = sg_s g_s and c0 = g . n* - g . <n>:
+  // from the forward's <n> with the context, else without cancellation from
+  // the flip moments, n*_s - <n_s> = -sg_s md_s / Z
   float gam[K];
 #pragma unroll
-  for (int s = 0; s < K; ++s) {
-    if ((bst >> s) & 1u) c0 += gs[s];
-    gam[s] = sgn[s] * gs[s];
+  for (int s = 0; s < K; ++s) gam[s] = sgn[s] * gs[s];
+  float c0 = 0.f;
+  if (use_ctx) {
+    c0 = gbase - gmean;
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+      if ((bst >> s) & 1u) c0 += gs[s];
+  } else {
+#pragma unroll
+    for (int s = 0; s < K; ++s) c0 = fmaf(-gam[s], md[s], c0);
+    c0 = active ? c0 / Z : 0.f;
   }
   // M(S) of the lane: its outer slots of S present, and the superset sum of
   // the inner ones
@@ -727,7 +788,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
   __syncwarp();
   const int L = contrib_len(n);
   float* my = s_contrib + team * L;
-  soft_contrib<K>(a, ts, q_s, my, s_contrib, sM, T, lt, kTeams, active, p);
+  soft_contrib<K>(a, ts, q_s, my, s_contrib, sM, T, lt, kTeams, active, p, lossp);
 }
 
 // Second stage: one block per contribution e sums the block partials --
@@ -754,11 +815,34 @@ static __global__ void __launch_bounds__(256) k_soft_reduce(SoftLaunch a, int nb
 // Third stage: the chain rule through M = Cdd^-1 and c = s Cgd V:
 //   dL/dCdd = -M (dL/dM) M,  dL/dCgd = s (S0 V0'^T + S1 (dx u)^T + S2 (dy w)^T)
 // with V0' = V0 + x0 u + y0 w and S0, S1, S2 the sums of dc, ix dc, iy dc.
+//
+// Fit step: then one Adam step on every parameter with its gradient, in the
+// update order of Kingma & Ba (Algorithm 1 of arXiv 1412.6980): m <- b1 m +
+// (1 - b1) g, v <- b2 v + (1 - b2) g^2, p <- p - lr (m / (1 - b1^t)) /
+// (sqrt(v / (1 - b2^t)) + eps); the loss = summed squared residuals / count.
+__device__ __forceinline__ void adam_update(const SoftLaunch& a, double* param, int e,
+                                            double g, double c1, double c2) {
+  const int cnt = a.n * a.n + a.n * a.ng;
+  double* mo = a.fit_state + e;
+  double* vo = a.fit_state + cnt + e;
+  const double m1 = a.beta1 * *mo + (1.0 - a.beta1) * g;
+  const double v1 = a.beta2 * *vo + (1.0 - a.beta2) * g * g;
+  *mo = m1;
+  *vo = v1;
+  *param -= a.lr * (m1 / c1) / (sqrt(v1 / c2) + a.eps);
+}
+
 static __global__ void k_soft_finalize(SoftLaunch a) {
   __shared__ double sG[kMaxDot * kMaxDot];
-  __shared__ double sS[3 * kMaxDot];
+  __shared__ double sS[3 * kMaxDot + 1];
   const int n = a.n, ng = a.ng;
   const int L = contrib_len(n);
+  const bool fit = a.fit_state != nullptr;
+  const int cnt = n * n + n * ng;
+  // the step count, read by every thread before thread 0 advances it
+  const double tstep = fit ? a.fit_state[2 * cnt] + 1.0 : 0.0;
+  const double c1 = fit ? 1.0 - pow(a.beta1, tstep) : 1.0;
+  const double c2 = fit ? 1.0 - pow(a.beta2, tstep) : 1.0;
   for (int e = threadIdx.x; e < L; e += blockDim.x) {
     const double v = a.sums[e];
     if (e < tri(n)) {
@@ -782,14 +866,22 @@ static __global__ void k_soft_finalize(SoftLaunch a) {
       for (int q = 0; q < n; ++q) t += sG[p * n + q] * M[q * n + j];
       s += M[i * n + p] * t;
     }
-    a.dL_dCdd[e] = -s;
+    if (a.dL_dCdd) a.dL_dCdd[e] = -s;
+    if (fit) adam_update(a, a.fit_Cdd + e, e, -s, c1, c2);
   }
   for (int e = threadIdx.x; e < n * ng; e += blockDim.x) {
     const int i = e / ng, g = e % ng;
     const double v0 = a.sc.V0[g] + a.sc.x0 * a.sc.u[g] + a.sc.y0 * a.sc.w[g];
     const double v = sS[i] * v0 + sS[n + i] * a.sc.dx * a.sc.u[g] +
                      sS[2 * n + i] * a.sc.dy * a.sc.w[g];
-    a.dL_dCgd[e] = a.mt.carrier * v;
+    const double gv = a.mt.carrier * v;
+    if (a.dL_dCgd) a.dL_dCgd[e] = gv;
+    if (fit) adam_update(a, a.fit_Cgd + e, n * n + e, gv, c1, c2);
+  }
+  if (a.loss_out && threadIdx.x == 0) *a.loss_out = (float)(sS[3 * n] * a.fit_inv_count);
+  if (fit) {
+    __syncthreads();
+    if (threadIdx.x == 0) a.fit_state[2 * cnt] = tstep;
   }
 }
 

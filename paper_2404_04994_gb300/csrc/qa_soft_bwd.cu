@@ -9,51 +9,58 @@ cudaError_t launch_soft_backward(const SoftLaunch& a, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// FP64 Cholesky inverse of a device Cdd (model update on the GPU).  One block,
-// everything staged in shared memory: warp 0 factors column by column (lane j
-// the pivot, the lanes below it one dot product each; the pivot's reciprocal
-// once, products after), threads j < n solve for column j of the inverse, and the symmetrisation, Cdd 1 and the 1-norm
-// condition number are spread over the block.
+// FP64 inverse of a device Cdd (model update on the GPU) by the symmetric
+// sweep operator (Gauss-Jordan elimination on diagonal pivots; Goodnight,
+// The American Statistician 33 (1979) 149).  Sweeping pivot k of a symmetric
+// matrix A with D = a_kk:
+//   a_kk <- -1/D,   a_ik = a_ki <- a_ik / D,   a_ij <- a_ij - a_ik a_kj / D,
+// and once every pivot is swept A holds -A^-1.  On a positive definite matrix
+// each pivot is a diagonal entry of a Schur complement, so D > 0; a pivot
+// <= 0 means Cdd is not positive definite.  One thread per entry (n^2 <=
+// 256) and two shared buffers, one barrier per pivot; the product a_ik a_kj
+// is the same for (i, j) and (j, i), so the result is exactly symmetric.
+// Warp 0 then forms the row sums Cdd 1, the 1-norm condition number and the
+// per-dot constants with shuffles; the block fills the FP32 / double-float
+// forms (same definitions as the host set-up).
 // ---------------------------------------------------------------------------
-__global__ void k_model_update(ModelData* md, int n, int ng, const double* Cdd,
-                               const double* Cgd) {
-  __shared__ double C[kMaxDot * kMaxDot], L[kMaxDot * kMaxDot], Ms[kMaxDot * kMaxDot];
-  __shared__ double rowsum[kMaxDot], colc[kMaxDot], colm[kMaxDot];
-  __shared__ double inv_diag[kMaxDot];  // 1 / L_jj: one FP64 division per column
-  __shared__ int ok;
+constexpr int kUpdThreads = kMaxDot * kMaxDot;
+
+__global__ void __launch_bounds__(kUpdThreads) k_model_update(ModelData* md, int n, int ng,
+                                                              const double* Cdd,
+                                                              const double* Cgd) {
+  __shared__ double A[2][kMaxDot * kMaxDot];
+  __shared__ double C[kMaxDot * kMaxDot];
   const int tid = threadIdx.x;
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
+  const int nn = n * n;
+  const int i = tid / n, j = tid % n;  // this thread's entry when tid < nn
+  if (tid < nn) {
     const double v = 0.5 * (Cdd[i * n + j] + Cdd[j * n + i]);
-    C[e] = v;
-    md->Cdd[e] = v;
-    L[e] = 0.0;
+    C[tid] = v;
+    A[0][tid] = v;
+    md->Cdd[tid] = v;
   }
   for (int e = tid; e < n * ng; e += blockDim.x) md->Cgd[e] = Cgd[e];
-  if (tid == 0) ok = 1;
   __syncthreads();
-  if (tid < 32) {
-    for (int j = 0; j < n; ++j) {
-      if (tid == j) {
-        double d = C[j * n + j];
-        for (int k = 0; k < j; ++k) d -= L[j * n + k] * L[j * n + k];
-        const double ljj = d > 0.0 ? sqrt(d) : 0.0;
-        L[j * n + j] = ljj;
-        inv_diag[j] = d > 0.0 ? 1.0 / ljj : 0.0;
-        if (!(d > 0.0)) ok = 0;
-      }
-      __syncwarp();
-      if (!(L[j * n + j] > 0.0)) break;
-      const double rjj = inv_diag[j];
-      if (tid > j && tid < n) {
-        double t = C[tid * n + j];
-        for (int k = 0; k < j; ++k) t -= L[tid * n + k] * L[j * n + k];
-        L[tid * n + j] = t * rjj;
-      }
-      __syncwarp();
+  bool ok = true;
+  for (int k = 0; k < n; ++k) {
+    const double* a = A[k & 1];
+    double* b = A[(k + 1) & 1];
+    const double D = a[k * n + k];  // the same value in every thread
+    if (!(D > 0.0)) {
+      ok = false;
+      break;
     }
+    if (tid < nn) {
+      const double r = 1.0 / D;
+      double v;
+      if (i == k && j == k) v = -r;
+      else if (i == k) v = a[k * n + j] * r;
+      else if (j == k) v = a[i * n + k] * r;
+      else v = fma(-(a[i * n + k] * a[k * n + j]), r, a[i * n + j]);
+      b[tid] = v;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (!ok) {
     if (tid == 0) {
       md->status = 1;
@@ -61,96 +68,80 @@ __global__ void k_model_update(ModelData* md, int n, int ng, const double* Cdd,
     }
     return;
   }
-  if (tid < n) {
-    const int col = tid;
-    double z[kMaxDot], y[kMaxDot];
-    for (int i = 0; i < n; ++i) {
-      double t = (i == col) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) t -= L[i * n + k] * z[k];
-      z[i] = t * inv_diag[i];
-    }
-    for (int i = n - 1; i >= 0; --i) {
-      double t = z[i];
-      for (int k = i + 1; k < n; ++k) t -= L[k * n + i] * y[k];
-      y[i] = t * inv_diag[i];
-    }
-    for (int i = 0; i < n; ++i) Ms[i * n + col] = y[i];
+  // M = -(swept A) into the buffer the last pivot read
+  double* Ms = A[(n + 1) & 1];
+  if (tid < nn) {
+    const double m = -A[n & 1][tid];
+    Ms[tid] = m;
+    md->M[tid] = m;
   }
   __syncthreads();
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    md->M[e] = 0.5 * (Ms[i * n + j] + Ms[j * n + i]);
-  }
-  if (tid < n) {
-    double r = 0.0, sc = 0.0, sm = 0.0;
-    for (int j = 0; j < n; ++j) {
-      r += C[tid * n + j];
-      sc += fabs(C[j * n + tid]);
-      sm += fabs(0.5 * (Ms[j * n + tid] + Ms[tid * n + j]));
-    }
-    rowsum[tid] = r;
-    colc[tid] = sc;
-    colm[tid] = sm;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double tot = 0.0, n1c = 0.0, n1m = 0.0;
-    for (int i = 0; i < n; ++i) {
-      tot += rowsum[i];
-      n1c = fmax(n1c, colc[i]);
-      n1m = fmax(n1m, colm[i]);
-    }
-    for (int i = 0; i < n; ++i) md->vs[i] = rowsum[i] / tot;
-    md->cond = n1c * n1m;
-    md->status = 0;
-  }
-  __syncthreads();
-  // FP32 / double-float forms (same definitions as the host set-up)
-  ModelConsts& k = md->k;
+  ModelConsts& kc = md->k;
   for (int e = tid; e < kMaxDot * kLdM; e += blockDim.x) {
-    const int i = e / kLdM, j = e % kLdM;
-    const bool live = i < n && j < n;
-    const df m = live ? df_from_double(md->M[i * n + j]) : df{0.f, 0.f};
-    k.Mhi[e] = m.hi;
-    k.Mlo[e] = m.lo;
-    const df cd = live ? df_from_double(md->Cdd[i * n + j]) : df{0.f, 0.f};
-    k.Cdd[e] = cd.hi;
-    k.CddLo[e] = cd.lo;
-  }
-  if (tid < kMaxDot) {
-    double r = 0.0;
-    for (int j = 0; j < n && tid < n; ++j) r += md->Cdd[tid * n + j];
-    k.sv[tid] = __double2float_rn(r);
-    k.sv2[tid] = tid < n ? df_from_double(r) : df{0.f, 0.f};
-    k.vs[tid] = tid < n ? df_from_double(md->vs[tid]) : df{0.f, 0.f};
-    // the same FP32 sum as the host set-up, from the same FP32 roundings
-    float al = 0.f;
-    if (tid < n) {
-      al = 0.5f * __double2float_rn(md->M[tid * n + tid]);
-      for (int j = 0; j < tid; ++j) al += fabsf(__double2float_rn(md->M[tid * n + j]));
+    const int r = e / kLdM, c = e % kLdM;
+    df m = {0.f, 0.f}, cd = {0.f, 0.f};
+    if (r < n && c < n) {
+      m = df_from_double(Ms[r * n + c]);
+      cd = df_from_double(C[r * n + c]);
     }
-    k.absl[tid] = al;
+    kc.Mhi[e] = m.hi;
+    kc.Mlo[e] = m.lo;
+    kc.Cdd[e] = cd.hi;
+    kc.CddLo[e] = cd.lo;
   }
-  if (tid == 0) {
-    double tot = 0.0;
-    for (int e = 0; e < n * n; ++e) tot += md->Cdd[e];
-    k.s_s = __double2float_rn(tot);
-    k.bx_qp_scale = __double2float_rn(8.0 * md->cond * (n + 1) * 5.9604644775390625e-8);
-    const double e1 = md->cond * (n + 1) * 5.9604644775390625e-8;
-    k.bx_qp_scale2 = __double2float_rn(8.0 * e1 * e1);
-    float qn = 0.f;  // from M itself (the other lanes' Mhi stores are not ordered yet)
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < i; ++j) qn += fminf(0.f, __double2float_rn(md->M[i * n + j]));
-    k.qneg = qn;
-    k.pad2[0] = k.pad2[1] = 0;
-    k.model_bad = md->status != 0;
-    k.pad = 0;
+  if (tid < 32) {
+    const bool live = tid < n;
+    double r = 0.0, sc = 0.0, sm = 0.0;
+    if (live)
+      for (int q = 0; q < n; ++q) {
+        r += C[tid * n + q];
+        sc += fabs(C[q * n + tid]);
+        sm += fabs(Ms[q * n + tid]);
+      }
+    double tot = r, n1c = sc, n1m = sm;
+    for (int off = 16; off > 0; off >>= 1) {
+      tot += __shfl_xor_sync(0xffffffffu, tot, off);
+      n1c = fmax(n1c, __shfl_xor_sync(0xffffffffu, n1c, off));
+      n1m = fmax(n1m, __shfl_xor_sync(0xffffffffu, n1m, off));
+    }
+    const double cond = n1c * n1m;
+    const double vsi = live ? r / tot : 0.0;
+    if (live) md->vs[tid] = vsi;
+    // the same FP32 sums as the host set-up, from the same FP32 roundings
+    float al = 0.f, qn = 0.f;
+    if (live) {
+      al = 0.5f * __double2float_rn(Ms[tid * n + tid]);
+      for (int q = 0; q < tid; ++q) {
+        const float mij = __double2float_rn(Ms[tid * n + q]);
+        al += fabsf(mij);
+        qn += fminf(0.f, mij);
+      }
+    }
+    if (tid < kMaxDot) {
+      kc.sv[tid] = __double2float_rn(r);
+      kc.sv2[tid] = live ? df_from_double(r) : df{0.f, 0.f};
+      kc.vs[tid] = live ? df_from_double(vsi) : df{0.f, 0.f};
+      kc.absl[tid] = al;
+    }
+    for (int off = 16; off > 0; off >>= 1) qn += __shfl_xor_sync(0xffffffffu, qn, off);
+    if (tid == 0) {
+      md->cond = cond;
+      md->status = 0;
+      kc.s_s = __double2float_rn(tot);
+      const double e1 = cond * (n + 1) * 5.9604644775390625e-8;
+      kc.bx_qp_scale = __double2float_rn(8.0 * e1);
+      kc.bx_qp_scale2 = __double2float_rn(8.0 * e1 * e1);
+      kc.qneg = qn;
+      kc.pad2[0] = kc.pad2[1] = 0;
+      kc.model_bad = 0;
+      kc.pad = 0;
+    }
   }
 }
 
 cudaError_t launch_model_update(ModelData* md, int n, int ng, const double* Cdd_dev,
                                 const double* Cgd_dev, cudaStream_t st) {
-  k_model_update<<<1, 32, 0, st>>>(md, n, ng, Cdd_dev, Cgd_dev);
+  k_model_update<<<1, kUpdThreads, 0, st>>>(md, n, ng, Cdd_dev, Cgd_dev);
   return cudaGetLastError();
 }
 

@@ -168,13 +168,32 @@ def test_autograd_function_and_fit_loop(qa):
     kT = 0.05
     target = qag.target_diagram(cfg["Cdd_target"], cfg["Cgd_target"], cfg["raster"], kT)
     fit = qag.CapacitanceFit(cfg["Cdd"], cfg["Cgd"], cfg["raster"], target, kT, lr=2e-3)
+    Ct, Gt = cfg["Cdd_target"], cfg["Cgd_target"]
+
+    def rel_err():
+        C = fit.Cdd.detach().cpu().numpy()
+        G = fit.Cgd.detach().cpu().numpy()
+        return (np.linalg.norm(C - Ct) / np.linalg.norm(Ct),
+                np.linalg.norm(G - Gt) / np.linalg.norm(Gt))
+
+    e0 = rel_err()
     losses = []
-    for _ in range(30):
+    for _ in range(100):
         fit.step()
         losses.append(float(fit.loss))
+    e1 = rel_err()
     fit.close()
+    print(f"fit: loss {losses[0]:.4g} -> {losses[-1]:.4g}; rel. error Cdd {e0[0]:.4f} -> "
+          f"{e1[0]:.4f}, Cgd {e0[1]:.4f} -> {e1[1]:.4f}")
     assert np.isfinite(losses).all()
-    assert losses[-1] < 0.7 * losses[1], losses[:3] + losses[-3:]
+    assert losses[-1] < 0.05 * losses[0], losses[:3] + losses[-3:]
+    # one raster of two swept gates does not determine every capacitance of
+    # an 8-dot grid (the other gates enter only through their summed offsets,
+    # dots the sweep barely moves only through their tails), so the diagram
+    # is fitted and Cgd moves toward the target model; the recovery of all
+    # capacitances is asserted where the raster determines them (the double
+    # dot of test_gpu_fit.py)
+    assert e1[1] < e0[1], (e0, e1)
     # the Function's gradient (backward from the forward's context) equals
     # the plain backward kernel's up to the FP32 rounding of <n>
     Cdd = torch.tensor(cfg["Cdd"], device="cuda", requires_grad=True)
