@@ -340,8 +340,9 @@ typedef struct {
  * qa_soft_occupation_backward, and one Adam step updates Cdd and Cgd in place.
  *   per_dot = 0: target DEVICE FP32 [H, W], L = mean_p (sum_i <n_i> - target_p)^2
  *   per_dot = 1: target DEVICE FP32 [H, W, n_dot], L = mean_{p,i} (<n_i> - target_pi)^2
- * opt_state: DEVICE FP64 [2 (n_dot^2 + n_dot n_gate) + 1], caller-owned and
- * zeroed before the first step (first moments, second moments, step count).
+ * opt_state: DEVICE FP64 [2 (n_dot^2 + n_dot n_gate) + 3], caller-owned and
+ * zeroed before the first step (first moments, second moments, then the step
+ * count t, beta1^t and beta2^t).
  * loss (DEVICE FP32 scalar), dL_dCdd, dL_dCgd (DEVICE FP64) and out_mean
  * (DEVICE FP32 [H, W, n_dot]) are optional outputs (NULL to skip), all taken
  * at the parameters before the update.  Everything is enqueued on `stream`

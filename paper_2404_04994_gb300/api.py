@@ -494,8 +494,8 @@ def qa_soft_occupation_backward_ctx(m, raster, kT, threshold, closed, n_charges,
 
 def fit_state_len(n, ng):
     """Doubles of qa_fit_step's optimiser state: first and second moments of
-    every parameter, then the step count."""
-    return 2 * (n * n + n * ng) + 1
+    every parameter, then the step count t, beta1^t and beta2^t."""
+    return 2 * (n * n + n * ng) + 3
 
 
 def qa_fit_step(m, raster, kT, threshold, closed, n_charges, target, per_dot, Cdd, Cgd,

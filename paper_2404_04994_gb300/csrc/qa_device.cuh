@@ -159,6 +159,7 @@ struct Counters {
   unsigned int q_search;
   unsigned int q_var[20];  // batched launch: the search queue of each kernel variant
   unsigned int lists_done; // blocks of the FP64 recheck kernel that have finished
+  unsigned int soft_done;  // blocks of the soft gradient reduction that have finished
 };
 
 // A single-array call's first kernel clears every counter but the two list

@@ -266,13 +266,14 @@ __device__ inline void soft_contrib(const SoftLaunch& a, TeamSlots& ts, const fl
   }
   if (lt == 0) my[L - 1] = active ? lossp : 0.f;
   __syncthreads();
-  // block sum over teams in fixed order (double-float), one partial per block
-  float* out = a.partials + (size_t)blockIdx.x * 2 * L;
+  // block sum over teams in fixed order (double-float), one partial per
+  // block, stored entry-major ([e][block]) so that the reduction of an entry
+  // reads its partials contiguously
+  float2* out = reinterpret_cast<float2*>(a.partials);
   for (int e = threadIdx.x; e < L; e += blockDim.x) {
     df sacc = {0.f, 0.f};
     for (int q = 0; q < teams; ++q) sacc = df_add(sacc, {s_contrib[q * L + e], 0.f});
-    out[2 * e] = sacc.hi;
-    out[2 * e + 1] = sacc.lo;
+    out[(size_t)e * gridDim.x + blockIdx.x] = make_float2(sacc.hi, sacc.lo);
   }
 }
 
@@ -791,35 +792,15 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
   soft_contrib<K>(a, ts, q_s, my, s_contrib, sM, T, lt, kTeams, active, p, lossp);
 }
 
-// Second stage: one block per contribution e sums the block partials --
-// thread j takes blocks j, j + 256, ... in order, then a fixed shared-memory
-// tree -- so the result does not depend on scheduling.
-static __global__ void __launch_bounds__(256) k_soft_reduce(SoftLaunch a, int nblocks) {
-  __shared__ df red[256];
-  const int e = blockIdx.x;
-  const int L = contrib_len(a.n);
-  df acc = {0.f, 0.f};
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-    const float* pb = a.partials + (size_t)b * 2 * L;
-    acc = df_add(acc, {pb[2 * e], pb[2 * e + 1]});
-  }
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int half = blockDim.x / 2; half > 0; half >>= 1) {
-    if ((int)threadIdx.x < half) red[threadIdx.x] = df_add(red[threadIdx.x], red[threadIdx.x + half]);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) a.sums[e] = df_to_double(red[0]);
-}
-
-// Third stage: the chain rule through M = Cdd^-1 and c = s Cgd V:
+// The chain rule through M = Cdd^-1 and c = s Cgd V, from the summed
+// contributions a.sums (one block, blockDim >= n^2):
 //   dL/dCdd = -M (dL/dM) M,  dL/dCgd = s (S0 V0'^T + S1 (dx u)^T + S2 (dy w)^T)
 // with V0' = V0 + x0 u + y0 w and S0, S1, S2 the sums of dc, ix dc, iy dc.
-//
 // Fit step: then one Adam step on every parameter with its gradient, in the
 // update order of Kingma & Ba (Algorithm 1 of arXiv 1412.6980): m <- b1 m +
 // (1 - b1) g, v <- b2 v + (1 - b2) g^2, p <- p - lr (m / (1 - b1^t)) /
-// (sqrt(v / (1 - b2^t)) + eps); the loss = summed squared residuals / count.
+// (sqrt(v / (1 - b2^t)) + eps), with b1^t, b2^t carried in the state; and the
+// loss = summed squared residuals / count.
 __device__ __forceinline__ void adam_update(const SoftLaunch& a, double* param, int e,
                                             double g, double c1, double c2) {
   const int cnt = a.n * a.n + a.n * a.ng;
@@ -832,19 +813,24 @@ __device__ __forceinline__ void adam_update(const SoftLaunch& a, double* param, 
   *param -= a.lr * (m1 / c1) / (sqrt(v1 / c2) + a.eps);
 }
 
-static __global__ void k_soft_finalize(SoftLaunch a) {
-  __shared__ double sG[kMaxDot * kMaxDot];
+__device__ __forceinline__ void soft_finalize_block(const SoftLaunch& a) {
+  __shared__ double sG[kMaxDot * kMaxDot], sMm[kMaxDot * kMaxDot], sT[kMaxDot * kMaxDot];
   __shared__ double sS[3 * kMaxDot + 1];
   const int n = a.n, ng = a.ng;
   const int L = contrib_len(n);
   const bool fit = a.fit_state != nullptr;
   const int cnt = n * n + n * ng;
-  // the step count, read by every thread before thread 0 advances it
-  const double tstep = fit ? a.fit_state[2 * cnt] + 1.0 : 0.0;
-  const double c1 = fit ? 1.0 - pow(a.beta1, tstep) : 1.0;
-  const double c2 = fit ? 1.0 - pow(a.beta2, tstep) : 1.0;
+  // step count and b1^t, b2^t (a zero state is step 0), read by every thread
+  // before thread 0 advances them
+  double tstep = 0.0, p1 = 1.0, p2 = 1.0;
+  if (fit) {
+    const double t0 = a.fit_state[2 * cnt];
+    tstep = t0 + 1.0;
+    p1 = (t0 > 0.0 ? a.fit_state[2 * cnt + 1] : 1.0) * a.beta1;
+    p2 = (t0 > 0.0 ? a.fit_state[2 * cnt + 2] : 1.0) * a.beta2;
+  }
   for (int e = threadIdx.x; e < L; e += blockDim.x) {
-    const double v = a.sums[e];
+    const double v = __ldcg(a.sums + e);
     if (e < tri(n)) {
       // e -> (i, j), i <= j
       int i = 0, rem = e;
@@ -856,18 +842,22 @@ static __global__ void k_soft_finalize(SoftLaunch a) {
       sS[e - tri(n)] = v;
     }
   }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) sMm[e] = a.md->M[e];
   __syncthreads();
-  const double* M = a.md->M;
+  // T = (dL/dM) M, then dL/dCdd = -M T: the same sums as -sum_p M_ip sum_q G_pq M_qj
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int p = e / n, j = e % n;
+    double t = 0.0;
+    for (int q = 0; q < n; ++q) t += sG[p * n + q] * sMm[q * n + j];
+    sT[e] = t;
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
     double s = 0.0;
-    for (int p = 0; p < n; ++p) {
-      double t = 0.0;
-      for (int q = 0; q < n; ++q) t += sG[p * n + q] * M[q * n + j];
-      s += M[i * n + p] * t;
-    }
+    for (int p = 0; p < n; ++p) s += sMm[i * n + p] * sT[p * n + j];
     if (a.dL_dCdd) a.dL_dCdd[e] = -s;
-    if (fit) adam_update(a, a.fit_Cdd + e, e, -s, c1, c2);
+    if (fit) adam_update(a, a.fit_Cdd + e, e, -s, 1.0 - p1, 1.0 - p2);
   }
   for (int e = threadIdx.x; e < n * ng; e += blockDim.x) {
     const int i = e / ng, g = e % ng;
@@ -876,13 +866,49 @@ static __global__ void k_soft_finalize(SoftLaunch a) {
                      sS[2 * n + i] * a.sc.dy * a.sc.w[g];
     const double gv = a.mt.carrier * v;
     if (a.dL_dCgd) a.dL_dCgd[e] = gv;
-    if (fit) adam_update(a, a.fit_Cgd + e, n * n + e, gv, c1, c2);
+    if (fit) adam_update(a, a.fit_Cgd + e, n * n + e, gv, 1.0 - p1, 1.0 - p2);
   }
   if (a.loss_out && threadIdx.x == 0) *a.loss_out = (float)(sS[3 * n] * a.fit_inv_count);
   if (fit) {
     __syncthreads();
-    if (threadIdx.x == 0) a.fit_state[2 * cnt] = tstep;
+    if (threadIdx.x == 0) {
+      a.fit_state[2 * cnt] = tstep;
+      a.fit_state[2 * cnt + 1] = p1;
+      a.fit_state[2 * cnt + 2] = p2;
+    }
   }
+}
+
+// Second stage: one block per contribution e sums the block partials --
+// thread j takes blocks j, j + 256, ... in order, then a fixed shared-memory
+// tree -- so the result does not depend on scheduling; the block that
+// finishes last (a counter, no waiting) then runs the chain rule above.
+static __global__ void __launch_bounds__(256) k_soft_reduce(SoftLaunch a, int nblocks) {
+  __shared__ df red[256];
+  __shared__ bool last;
+  const int e = blockIdx.x;
+  const float2* pe = reinterpret_cast<const float2*>(a.partials) + (size_t)e * nblocks;
+  df acc = {0.f, 0.f};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    const float2 v = pe[b];
+    acc = df_add(acc, {v.x, v.y});
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int half = blockDim.x / 2; half > 0; half >>= 1) {
+    if ((int)threadIdx.x < half) red[threadIdx.x] = df_add(red[threadIdx.x], red[threadIdx.x + half]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.sums[e] = df_to_double(red[0]);
+    __threadfence();
+    last = atomicAdd(&a.cnt->soft_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  soft_finalize_block(a);
+  if (threadIdx.x == 0) a.cnt->soft_done = 0u;  // zero again for the next call
 }
 
 inline size_t soft_partials_floats_impl(int n, long long P, const SearchCfg& cfg) {
@@ -905,10 +931,7 @@ static cudaError_t run_soft(const SoftLaunch& a, cudaStream_t st) {
   }
   if (a.ev) cudaEventRecord(a.ev[0], st);
   k_soft<L1, L2, CLOSED, BWD, KMAX><<<grid, kSoftThreads, smem, st>>>(a);
-  if (BWD) {
-    k_soft_reduce<<<contrib_len(a.n), 256, 0, st>>>(a, (int)grid);
-    k_soft_finalize<<<1, 256, 0, st>>>(a);
-  }
+  if (BWD) k_soft_reduce<<<contrib_len(a.n), 256, 0, st>>>(a, (int)grid);
   if (a.ev) cudaEventRecord(a.ev[1], st);
   return cudaGetLastError();
 }
@@ -923,10 +946,7 @@ static cudaError_t run_soft_dense(const SoftLaunch& a, cudaStream_t st) {
   const size_t smem = BWD ? (size_t)teams * contrib_len(a.n) * sizeof(float) : 0;
   if (a.ev) cudaEventRecord(a.ev[0], st);
   k_soft_dense<CLOSED, BWD><<<grid, kSoftThreads, smem, st>>>(a);
-  if (BWD) {
-    k_soft_reduce<<<contrib_len(a.n), 256, 0, st>>>(a, (int)grid);
-    k_soft_finalize<<<1, 256, 0, st>>>(a);
-  }
+  if (BWD) k_soft_reduce<<<contrib_len(a.n), 256, 0, st>>>(a, (int)grid);
   if (a.ev) cudaEventRecord(a.ev[1], st);
   return cudaGetLastError();
 }

@@ -54,7 +54,11 @@ def test_fused_steps_match_autograd_and_torch_adam(qa):
                                    rtol=0, atol=1e-6)
         np.testing.assert_allclose(a.Cgd.detach().cpu().numpy(), b.Cgd.detach().cpu().numpy(),
                                    rtol=0, atol=1e-6)
-    assert int(a.state[-1].item()) == 8
+    cnt = 8 * 8 + 8 * 8
+    st = a.state.cpu().numpy()
+    assert st[2 * cnt] == 8.0
+    assert st[2 * cnt + 1] == pytest.approx(0.9 ** 8, rel=1e-14)
+    assert st[2 * cnt + 2] == pytest.approx(0.999 ** 8, rel=1e-14)
     a.close()
     b.close()
 
@@ -147,7 +151,8 @@ def test_fused_step_outputs_equal_the_separate_calls(qa, closed, per_dot):
         np.testing.assert_allclose(p1.cpu().numpy(), want, rtol=0, atol=1e-12)
     st = state.cpu().numpy()
     np.testing.assert_allclose(st[:n * n], (1 - b1) * dC.cpu().numpy().ravel(), rtol=1e-15)
-    assert st[-1] == 1.0
+    cnt = n * n + n * ng
+    assert list(st[2 * cnt:]) == [1.0, b1, b2]
     with pytest.raises(qa.QAError):
         qa.qa_fit_step(m.handle, ras, kT, t, closed, N, target, per_dot, Cdd, Cgd, state, -1.0)
     with pytest.raises(qa.QAError):
