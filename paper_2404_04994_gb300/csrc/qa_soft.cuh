@@ -62,49 +62,59 @@ __device__ __forceinline__ float delta_energy(const TeamSlots& ts, const float* 
   return D;
 }
 
-// Fit step, lane 0 of a team: the pixel's <n> from the slot weight sums
-// accb (slot order) and Z, then the MSE gradient g = dL/d<n> into gsh[0, n)
-// and the pixel's squared residual into lossp.  Sum target: residual r =
-// sum_i <n_i> - target_p and g_i = scale r for every dot; per-dot target:
-// r_i = <n_i> - target_pi and g_i = scale r_i.
+// v[s] for a runtime s, the array staying in registers.
 template <int K>
-__device__ __forceinline__ void fit_loss_grad(const SoftLaunch& a, const TeamSlots& ts,
-                                              const float* accb, float Z, long long p,
-                                              float* gsh, float& lossp) {
-  const int n = a.n;
-  float pred = 0.f;
-  for (int i = 0; i < n; ++i) {
-    float v = (float)ts.base[i];
-    if ((ts.mask >> i) & 1u) {
-      const int s = __popc(ts.mask & ((1u << i) - 1u));
+__device__ __forceinline__ float pick(const float (&v)[K], int s) {
+  float r = 0.f;
 #pragma unroll
-      for (int q = 0; q < K; ++q)
-        if (q == s) v += accb[q] / Z;
+  for (int q = 0; q < K; ++q)
+    if (q == s) r = v[q];
+  return r;
+}
+
+// Fit step: the pixel's <n> from the slot weight sums accb (slot order) and
+// Z, then the MSE gradient g = dL/d<n> into gsh[0, n); returns the pixel's
+// squared residual (summed over the team).  Sum target: r = sum_i <n_i> -
+// target_p and g_i = scale r for every dot; per-dot target: r_i = <n_i> -
+// target_pi and g_i = scale r_i.  The team's lanes take the dots; all lanes
+// of the warp call.
+template <int K>
+__device__ __forceinline__ float fit_loss_grad_team(const SoftLaunch& a, const TeamSlots& ts,
+                                                    const float (&accb)[K], float Z,
+                                                    long long p, float* gsh, int lt, int T,
+                                                    bool active) {
+  const int n = a.n;
+  float part = 0.f;
+  if (active)
+    for (int i = lt; i < n; i += T) {
+      float v = (float)ts.base[i];
+      if ((ts.mask >> i) & 1u) v += pick<K>(accb, __popc(ts.mask & ((1u << i) - 1u))) / Z;
+      if (a.out_mean) a.out_mean[p * n + i] = v;
+      if (a.fit_per_dot) {
+        const float r = v - a.fit_target[p * n + i];
+        gsh[i] = a.fit_scale * r;
+        part = fmaf(r, r, part);
+      } else {
+        part += v;
+      }
     }
-    gsh[i] = v;
-    if (a.out_mean) a.out_mean[p * n + i] = v;
-    pred += v;
+  for (int off = 1; off < T; off <<= 1) part += __shfl_xor_sync(kFullS, part, off);
+  float lossp = part;
+  if (!a.fit_per_dot) {
+    const float r = active ? part - a.fit_target[p] : 0.f;
+    if (active)
+      for (int i = lt; i < n; i += T) gsh[i] = a.fit_scale * r;
+    lossp = r * r;
   }
-  float l = 0.f;
-  if (a.fit_per_dot) {
-    for (int i = 0; i < n; ++i) {
-      const float r = gsh[i] - a.fit_target[p * n + i];
-      l = fmaf(r, r, l);
-      gsh[i] = a.fit_scale * r;
-    }
-  } else {
-    const float r = pred - a.fit_target[p];
-    l = r * r;
-    for (int i = 0; i < n; ++i) gsh[i] = a.fit_scale * r;
-  }
-  lossp = l;
+  __syncwarp();
+  return active ? lossp : 0.f;
 }
 
 // Lane 0 of a team: pixel p's record into the team's slots (slot order: the
 // s-th ambiguous dot; h[] reused slot-ordered).  A pixel whose FP32 candidate
 // set may differ from the exact one is prepared again in FP64.
 template <bool CLOSED>
-__device__ inline void soft_setup(const SoftLaunch& a, TeamSlots& ts, long long p) {
+__device__ __noinline__ void soft_setup(const SoftLaunch& a, TeamSlots& ts, long long p) {
   const int n = a.n;
   const PixRec& rec = a.recs[p];
   unsigned mask = rec.mask;
@@ -156,6 +166,38 @@ __device__ inline void soft_setup(const SoftLaunch& a, TeamSlots& ts, long long 
   ts.mask = mask;
   ts.k = s;
   ts.w = CLOSED ? w : -1;
+}
+
+// The same, the team's lanes splitting the dots of the common case (the FP64
+// redo of a doubtful pixel stays with lane 0); all lanes of the warp call.
+template <bool CLOSED>
+__device__ inline void soft_setup_team(const SoftLaunch& a, TeamSlots& ts, long long p, int lt,
+                                       int T, bool active) {
+  if (active) {
+    const PixRec& rec = a.recs[p];
+    if (rec.flags & (kFlagBoundary | kFlagQPCap)) {
+      if (lt == 0) soft_setup<CLOSED>(a, ts, p);
+    } else {
+      const int n = a.n;
+      const unsigned mask = rec.mask;
+      for (int i = lt; i < n; i += T) {
+        ts.base[i] = rec.base[i];
+        ts.chi[i] = rec.chi[i];
+        ts.clo[i] = rec.clo[i];
+        if ((mask >> i) & 1u) {
+          const int s = __popc(mask & ((1u << i) - 1u));
+          ts.dot[s] = i;
+          ts.h[s] = rec.h[i];  // h[] slot-ordered
+        }
+      }
+      if (lt == 0) {
+        ts.mask = mask;
+        ts.k = __popc(mask);
+        ts.w = CLOSED ? rec.w : -1;
+      }
+    }
+  }
+  __syncwarp();
 }
 
 // The gradient at b* (gp / gm of every slot) and U(b*) / kT in double-float,
@@ -301,8 +343,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
   TeamSlots& ts = tsm[team];
   const float kT = (float)a.kT;
 
-  if (active && lt == 0) soft_setup<CLOSED>(a, ts, p);
-  __syncwarp();
+  soft_setup_team<CLOSED>(a, ts, p, lt, T, active);
   float* Ms = slotM[team];
   if (active)
     for (int e = lt; e < KMAX * KMAX; e += T) {
@@ -389,10 +430,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft(SoftLaunch a) {
   for (int s = 0; s < KMAX; ++s) gs[s] = 0.f;
   const bool fit = a.fit_target != nullptr;
   float lossp = 0.f;
-  if (fit) {
-    if (active && lt == 0) fit_loss_grad<KMAX>(a, ts, acc, Z, p, sGf[team], lossp);
-    __syncwarp();
-  }
+  if (fit) lossp = fit_loss_grad_team<KMAX>(a, ts, acc, Z, p, sGf[team], lt, T, active);
   if (active) {
     const float* g = fit ? sGf[team] : a.grad_mean + p * n;
     for (int i = 0; i < n; ++i) gbase += g[i] * (float)ts.base[i];
@@ -490,6 +528,52 @@ constexpr int kDenseT = 8;    // lanes per pixel
 constexpr int kDenseIn = 5;   // inner slots: a table of 32 patterns
 constexpr int kDenseMax = 8;  // slots
 
+constexpr int kMom = 1 + kDenseMax + tri(kDenseMax - 1);  // |S| <= 2 moments: 37
+constexpr int kMomPad = 40;                                 // ... padded to 5 per lane
+
+// Superset sum over NB bits in place: w[S] <- sum over b containing S of w[b].
+template <int NB>
+__device__ __forceinline__ void superset_sum(float (&w)[1 << NB]) {
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+#pragma unroll
+    for (int b = 0; b < (1 << NB); ++b)
+      if (!((b >> j) & 1)) w[b] += w[b | (1 << j)];
+}
+
+// Sum of X[0, N) over a team of 8 lanes, scattered: three halving exchanges
+// (partners 4, 2, 1), after which each lane holds N / 8 of the sums, written
+// to out[] where the index is below nout.  All lanes of the warp call.
+template <int N>
+__device__ __forceinline__ void team_reduce_scatter8(float (&X)[N], int lt, float* out,
+                                                     int nout) {
+  static_assert(N % 8 == 0, "N must be a multiple of 8");
+  constexpr int H1 = N / 2, H2 = N / 4, H3 = N / 8;
+  const bool b2 = (lt >> 2) & 1, b1 = (lt >> 1) & 1, b0 = lt & 1;
+#pragma unroll
+  for (int i = 0; i < H1; ++i) {
+    const float send = b2 ? X[i] : X[H1 + i];
+    const float keep = b2 ? X[H1 + i] : X[i];
+    X[i] = keep + __shfl_xor_sync(kFullS, send, 4);
+  }
+#pragma unroll
+  for (int i = 0; i < H2; ++i) {
+    const float send = b1 ? X[i] : X[H2 + i];
+    const float keep = b1 ? X[H2 + i] : X[i];
+    X[i] = keep + __shfl_xor_sync(kFullS, send, 2);
+  }
+#pragma unroll
+  for (int i = 0; i < H3; ++i) {
+    const float send = b0 ? X[i] : X[H3 + i];
+    const float keep = b0 ? X[H3 + i] : X[i];
+    X[i] = keep + __shfl_xor_sync(kFullS, send, 1);
+  }
+  const int base = (b2 ? H1 : 0) + (b1 ? H2 : 0) + (b0 ? H3 : 0);
+#pragma unroll
+  for (int i = 0; i < H3; ++i)
+    if (base + i < nout) out[base + i] = X[i];
+}
+
 // F of the 32 inner patterns for the lane's outer pattern tout (slots 5..7).
 // G / sg per slot, Ms the team's slot-ordered M (zero beyond the k slots,
 // where G is kBig so that no pattern using such a slot counts).
@@ -543,22 +627,60 @@ __device__ __forceinline__ void dense_table(const float* G, const float* sg, con
   for (int b = 1; b < NI; ++b) F[b] += P[b];
 }
 
-template <bool CLOSED, bool BWD>
-__global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
+// Threads per block of the dense kernel; its per-team arrays live in one
+// dynamic shared buffer laid out by DenseSmem.
+#ifndef QA_DENSE_THREADS
+#define QA_DENSE_THREADS 128
+#endif
+constexpr int kDenseThreads = QA_DENSE_THREADS;
+static_assert(kDenseThreads % 32 == 0 && kDenseThreads <= 1024 && kDenseThreads >= kSoftThreads,
+              "dense block size (the partials are sized for kSoftThreads)");
+
+__host__ __device__ constexpr size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+struct DenseSmem {
+  size_t slots, slotM, qa, qd, gf, wr, contrib, total;
+  __host__ __device__ constexpr DenseSmem(bool bwd, int L)
+      : slots(0),
+        slotM(al16(sizeof(TeamSlots) * (kDenseThreads / kDenseT))),
+        qa(slotM + al16(sizeof(float) * (kDenseThreads / kDenseT) * kDenseMax * kDenseMax)),
+        qd(qa + (bwd ? al16(sizeof(float) * (kDenseThreads / kDenseT) * (tri(kDenseMax) + kDenseMax + 1)) : 0)),
+        gf(qd + (bwd ? al16(sizeof(float) * (kDenseThreads / kDenseT) * kMom) : 0)),
+        wr(gf + (bwd ? al16(sizeof(float) * (kDenseThreads / kDenseT) * kMaxDot) : 0)),
+        contrib(wr + (bwd ? al16(sizeof(float) * kDenseThreads * ((1 << kDenseIn) + 4)) : 0)),
+        total(contrib + (bwd ? al16(sizeof(float) * (kDenseThreads / kDenseT) * L) : 0)) {}
+};
+
+// what a launch of the dense kernel computes: the forward; the backward from
+// grad_mean; the backward given the forward's context; the fused fit step
+enum DenseMode { kDenseFwd = 0, kDenseBwd = 1, kDenseBwdCtx = 2, kDenseFit = 3 };
+
+// five blocks of 128 threads per SM: at most 102 registers a thread
+template <bool CLOSED, int MODE>
+__global__ void __launch_bounds__(kDenseThreads, 640 / kDenseThreads) k_soft_dense(SoftLaunch a) {
+  constexpr bool BWD = MODE != kDenseFwd;
   constexpr int K = kDenseMax, NI = 1 << kDenseIn;
-  constexpr int kTeams = kSoftThreads / kDenseT;
-  __shared__ ModelConsts cs;
-  __shared__ TeamSlots tsm[kTeams];
-  __shared__ float slotM[kTeams][K * K];
-  __shared__ float sQa[BWD ? kTeams : 1][tri(K) + K + 1];  // Qa, va, sa of a team
-  __shared__ float sQd[BWD ? kTeams : 1][1 + K + tri(K - 1)];  // the same in flip coordinates
-  __shared__ float sGf[BWD ? kTeams : 1][kMaxDot];             // fit step: g of a team
-  extern __shared__ float s_contrib[];                     // BWD: [teams][contrib_len]
+  constexpr int kTeams = kDenseThreads / kDenseT;
+  // of the model constants only M as double-float (hi, lo)
+  __shared__ __align__(16) float sMh[kMaxDot * kLdM], sMl[kMaxDot * kLdM];
+  extern __shared__ __align__(16) unsigned char s_dyn[];
   const int n = a.n;
-  stage_consts(&a.md->k, &cs);
+  const DenseSmem lay(BWD, contrib_len(n));
+  TeamSlots* tsm = reinterpret_cast<TeamSlots*>(s_dyn + lay.slots);
+  float* slotM = reinterpret_cast<float*>(s_dyn + lay.slotM);  // [team][K * K]
+  float* sQa = reinterpret_cast<float*>(s_dyn + lay.qa);       // [team][tri(K) + K + 1]: Qa, va, sa
+  float* sQd = reinterpret_cast<float*>(s_dyn + lay.qd);       // [team][kMom]: the same, flip coords
+  float* sGf = reinterpret_cast<float*>(s_dyn + lay.gf);       // [team][kMaxDot]: fit step g
+  float* sWr = reinterpret_cast<float*>(s_dyn + lay.wr);       // [thread][NI + 4]: raw weights
+  float* s_contrib = reinterpret_cast<float*>(s_dyn + lay.contrib);  // [team][contrib_len]
+  static_assert((kMaxDot * kLdM) % 4 == 0, "float4 staging");
+  for (int e = threadIdx.x; e < kMaxDot * kLdM / 4; e += blockDim.x) {
+    reinterpret_cast<float4*>(sMh)[e] = reinterpret_cast<const float4*>(a.md->k.Mhi)[e];
+    reinterpret_cast<float4*>(sMl)[e] = reinterpret_cast<const float4*>(a.md->k.Mlo)[e];
+  }
   __syncthreads();
-  const float* sM = cs.Mhi;
-  const float* sMlo = cs.Mlo;
+  const float* sM = sMh;
+  const float* sMlo = sMl;
   const int T = kDenseT;
   const int team = threadIdx.x / T, lt = threadIdx.x % T;
   const long long p = (long long)blockIdx.x * kTeams + team;
@@ -566,9 +688,8 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
   TeamSlots& ts = tsm[team];
   const float kT = (float)a.kT;
 
-  if (active && lt == 0) soft_setup<CLOSED>(a, ts, p);
-  __syncwarp();
-  float* Ms = slotM[team];
+  soft_setup_team<CLOSED>(a, ts, p, lt, T, active);
+  float* Ms = slotM + team * (K * K);
   if (active)
     for (int e = lt; e < K * K; e += T) {
       const int s = e / K, s2 = e % K;
@@ -582,7 +703,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
   const int wcl = (CLOSED && active) ? ts.w : 0;
 
   // pass 1: b* (from the forward's context when the backward has it)
-  const bool use_ctx = BWD && a.ctx_in != nullptr;
+  constexpr bool use_ctx = MODE == kDenseBwdCtx;
   unsigned b1 = 0u;
   if (use_ctx) {
     if (active) b1 = a.ctx_in[p].x;
@@ -638,11 +759,14 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
       w[b] = ok ? exp2f(c2 * w[b]) : 0.f;
     }
   }
+  // the backward needs the raw weights again once the gradient is known
+  float* wraw = sWr + threadIdx.x * (NI + 4);
+  if (BWD) {
 #pragma unroll
-  for (int j = 0; j < kDenseIn; ++j)
-#pragma unroll
-    for (int b = 0; b < NI; ++b)
-      if (!((b >> j) & 1)) w[b] += w[b | (1 << j)];
+    for (int b = 0; b < NI; b += 4)
+      *reinterpret_cast<float4*>(wraw + b) = make_float4(w[b], w[b + 1], w[b + 2], w[b + 3]);
+  }
+  superset_sum<kDenseIn>(w);
   // the lane's outer slots present (1) or absent (0)
   float po[K - kDenseIn];
 #pragma unroll
@@ -666,12 +790,7 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
     if (active) {
       for (int i = lt; i < n; i += T) {
         float v = (float)ts.base[i];
-        if ((ts.mask >> i) & 1u) {
-          const int s = __popc(ts.mask & ((1u << i) - 1u));
-#pragma unroll
-          for (int q = 0; q < K; ++q)
-            if (q == s) v += accb[q] / Z;
-        }
+        if ((ts.mask >> i) & 1u) v += pick<K>(accb, __popc(ts.mask & ((1u << i) - 1u))) / Z;
         a.out_mean[p * n + i] = v;
       }
       if (lt == 0 && a.out_logZ) a.out_logZ[p] = logf(Z) - ts.ustar_kT;
@@ -680,19 +799,17 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
     return;
   }
 
-  // ---- backward: the moments of a_b in flip coordinates, per lane ----
+  // ---- backward: the moments of a_b in flip coordinates ----
   float gs[K];
   float gbase = 0.f, gmean = 0.f;
 #pragma unroll
   for (int s = 0; s < K; ++s) gs[s] = 0.f;
-  const bool fit = a.fit_target != nullptr;
+  constexpr bool fit = MODE == kDenseFit;
   float lossp = 0.f;
-  if (fit) {
-    if (active && lt == 0) fit_loss_grad<K>(a, ts, accb, Z, p, sGf[team], lossp);
-    __syncwarp();
-  }
+  float* gf = sGf + team * kMaxDot;
+  if (fit) lossp = fit_loss_grad_team<K>(a, ts, accb, Z, p, gf, lt, T, active);
   if (active) {
-    const float* g = fit ? sGf[team] : a.grad_mean + p * n;
+    const float* g = fit ? gf : a.grad_mean + p * n;
 #pragma unroll
     for (int s = 0; s < K; ++s)
       if (s < k) gs[s] = g[ts.dot[s]];
@@ -718,73 +835,83 @@ __global__ void __launch_bounds__(kSoftThreads) k_soft_dense(SoftLaunch a) {
     for (int s = 0; s < K; ++s) c0 = fmaf(-gam[s], md[s], c0);
     c0 = active ? c0 / Z : 0.f;
   }
-  // M(S) of the lane: its outer slots of S present, and the superset sum of
-  // the inner ones
-  auto Mx = [&](unsigned S) -> float {
-    float v = w[S & (unsigned)(NI - 1)];
-#pragma unroll
-    for (int i = 0; i < K - kDenseIn; ++i)
-      if ((S >> (kDenseIn + i)) & 1u) v *= po[i];
-    return v;
-  };
-  // each moment summed over the team as soon as it is formed (few live
-  // accumulators), kept by lane 0 in the team's row of sQd: sa, vd[K], then
-  // Qd[s < s2] at s * (2K - s - 1) / 2 + (s2 - s - 1)
-  float* qd = sQd[team];
-  auto team_sum = [&](float v) {
-    for (int off = 1; off < T; off <<= 1) v += __shfl_xor_sync(kFullS, v, off);
-    return v;
-  };
+  // sum_d w(d) (c0 + gam . d) d_S = c0 M(S) + Y(S): Y from y(d) = w(d) gam . d
+  // by the same superset sum over the inner bits (gam . d = go + the inner
+  // slots' gam by doubling); the outer slots of S count where the lane has them
+  float y[NI];
   {
-    float v = c0 * Mx(0u);
+    float go = 0.f;
 #pragma unroll
-    for (int j = 0; j < K; ++j) v = fmaf(gam[j], Mx(1u << j), v);
-    v = team_sum(v);
-    if (lt == 0) qd[0] = v;
+    for (int i = 0; i < K - kDenseIn; ++i) go = fmaf(po[i], gam[kDenseIn + i], go);
+    y[0] = go;
+#pragma unroll
+    for (int j = 0; j < kDenseIn; ++j)
+#pragma unroll
+      for (int b = 0; b < (1 << j); ++b) y[b | (1 << j)] = y[b] + gam[j];
+#pragma unroll
+    for (int b = 0; b < NI; b += 4) {
+      const float4 r = *reinterpret_cast<const float4*>(wraw + b);
+      y[b] *= r.x;
+      y[b + 1] *= r.y;
+      y[b + 2] *= r.z;
+      y[b + 3] *= r.w;
+    }
   }
+  superset_sum<kDenseIn>(y);
+  // the 37 moments X(S), |S| <= 2, in the order sa, vd[K], Qd[s < s2], padded
+  // to kMomPad, then summed over the team by a reduce-scatter
+  float X[kMomPad];
+  auto mom = [&](unsigned S) -> float {
+    const unsigned si = S & (unsigned)(NI - 1), so = S >> kDenseIn;
+    const float v = fmaf(c0, w[si], y[si]);
+    return (so & ~tout) == 0u && lane_on ? v : 0.f;
+  };
+  X[0] = mom(0u);
 #pragma unroll
-  for (int s = 0; s < K; ++s) {
-    float v = c0 * Mx(1u << s);
-#pragma unroll
-    for (int j = 0; j < K; ++j) v = fmaf(gam[j], Mx((1u << s) | (1u << j)), v);
-    v = team_sum(v);
-    if (lt == 0) qd[1 + s] = v;
-  }
+  for (int s = 0; s < K; ++s) X[1 + s] = mom(1u << s);
 #pragma unroll
   for (int s = 0; s < K; ++s)
 #pragma unroll
-    for (int s2 = s + 1; s2 < K; ++s2) {
-      const unsigned S = (1u << s) | (1u << s2);
-      float v = c0 * Mx(S);
+    for (int s2 = s + 1; s2 < K; ++s2)
+      X[1 + K + s * (2 * K - s - 1) / 2 + (s2 - s - 1)] = mom((1u << s) | (1u << s2));
 #pragma unroll
-      for (int j = 0; j < K; ++j) v = fmaf(gam[j], Mx(S | (1u << j)), v);
-      v = team_sum(v);
-      if (lt == 0) qd[1 + K + s * (2 * K - s - 1) / 2 + (s2 - s - 1)] = v;
-    }
+  for (int q = kMom; q < kMomPad; ++q) X[q] = 0.f;
+  float* qd = sQd + team * kMom;
+  team_reduce_scatter8<kMomPad>(X, lt, qd, kMom);
+  __syncwarp();
   // scale by -1 / (kT Z) and turn to charge coordinates, n_s = n*_s + sg_s d_s:
   //   va_s = bt_s sa + sg_s vd_s,  Qa_ss = va_s,
   //   Qa_ss' = bt_s bt_s' sa + bt_s sg_s' vd_s' + bt_s' sg_s vd_s + sg_s sg_s' Qd_ss'
+  // (the team's lanes split the entries)
   const float alpha = active ? -1.0f / (kT * Z) : 0.f;
-  float* q_s = sQa[BWD ? team : 0];
-  if (lt == 0) {
+  float* q_s = sQa + team * (tri(K) + K + 1);
+  {
     const float sa_a = alpha * qd[0];
-#pragma unroll
-    for (int s = 0; s < K; ++s) {
+    for (int e = lt; e < tri(K); e += T) {
+      int s = 0, rem = e;
+      while (rem >= K - s) { rem -= K - s; ++s; }
+      const int s2 = s + rem;
       const float bts = ((bst >> s) & 1u) ? 1.f : 0.f;
+      const float sgs = ((bst >> s) & 1u) ? -1.f : 1.f;
       const float vs = alpha * qd[1 + s];
-      const float va = bts * sa_a + sgn[s] * vs;
-      q_s[s * K - s * (s - 1) / 2] = va;
-      q_s[tri(K) + s] = va;
-#pragma unroll
-      for (int s2 = s + 1; s2 < K; ++s2) {
+      float q;
+      if (s2 == s) {
+        q = bts * sa_a + sgs * vs;
+      } else {
         const float bt2 = ((bst >> s2) & 1u) ? 1.f : 0.f;
+        const float sg2 = ((bst >> s2) & 1u) ? -1.f : 1.f;
         const float v2 = alpha * qd[1 + s2];
-        q_s[s * K - s * (s - 1) / 2 + (s2 - s)] =
-            bts * bt2 * sa_a + bts * sgn[s2] * v2 + bt2 * sgn[s] * vs +
-            sgn[s] * sgn[s2] * alpha * qd[1 + K + s * (2 * K - s - 1) / 2 + (s2 - s - 1)];
+        q = bts * bt2 * sa_a + bts * sg2 * v2 + bt2 * sgs * vs +
+            sgs * sg2 * alpha * qd[1 + K + s * (2 * K - s - 1) / 2 + (s2 - s - 1)];
       }
+      q_s[e] = q;
     }
-    q_s[tri(K) + K] = sa_a;
+    for (int s = lt; s < K; s += T) {
+      const float bts = ((bst >> s) & 1u) ? 1.f : 0.f;
+      const float sgs = ((bst >> s) & 1u) ? -1.f : 1.f;
+      q_s[tri(K) + s] = bts * sa_a + sgs * alpha * qd[1 + s];
+    }
+    if (lt == 0) q_s[tri(K) + K] = sa_a;
   }
   __syncwarp();
   const int L = contrib_len(n);
@@ -912,6 +1039,8 @@ static __global__ void __launch_bounds__(256) k_soft_reduce(SoftLaunch a, int nb
 }
 
 inline size_t soft_partials_floats_impl(int n, long long P, const SearchCfg& cfg) {
+  // blocks of the launch that has the most (the dense kernel's blocks hold
+  // at least as many teams as the per-candidate kernel's)
   const int teams = kSoftThreads / cfg.T;
   const long long blocks = (P + teams - 1) / teams;
   return (size_t)blocks * 2 * (size_t)contrib_len(n);
@@ -938,17 +1067,44 @@ static cudaError_t run_soft(const SoftLaunch& a, cudaStream_t st) {
 
 // Dense form (up to 8 dots; teams of kDenseT lanes, the host sizes the
 // partials for cfg.T = kDenseT).
-template <bool CLOSED, bool BWD>
+template <bool CLOSED, int MODE>
 static cudaError_t run_soft_dense(const SoftLaunch& a, cudaStream_t st) {
-  constexpr int teams = kSoftThreads / kDenseT;
+  constexpr bool BWD = MODE != kDenseFwd;
+  constexpr int teams = kDenseThreads / kDenseT;
   const long long P = a.sc.P;
   const unsigned grid = (unsigned)((P + teams - 1) / teams);
-  const size_t smem = BWD ? (size_t)teams * contrib_len(a.n) * sizeof(float) : 0;
+  const size_t smem = DenseSmem(BWD, contrib_len(a.n)).total;
+  // the largest buffer (n = 16 does not come here: at most contrib_len(8)),
+  // and the whole carveout so that as many blocks as the registers allow fit
+  // an SM (once per process)
+  static const cudaError_t attr = [] {
+    cudaError_t e = cudaFuncSetAttribute(k_soft_dense<CLOSED, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)DenseSmem(BWD, contrib_len(kDenseMax)).total);
+    if (e == cudaSuccess &&
+        cudaFuncSetAttribute(k_soft_dense<CLOSED, MODE>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+      cudaGetLastError();  // the carveout is only a preference
+    return e;
+  }();
+  if (attr != cudaSuccess) return attr;
   if (a.ev) cudaEventRecord(a.ev[0], st);
-  k_soft_dense<CLOSED, BWD><<<grid, kSoftThreads, smem, st>>>(a);
+  k_soft_dense<CLOSED, MODE><<<grid, kDenseThreads, smem, st>>>(a);
   if (BWD) k_soft_reduce<<<contrib_len(a.n), 256, 0, st>>>(a, (int)grid);
   if (a.ev) cudaEventRecord(a.ev[1], st);
   return cudaGetLastError();
+}
+
+template <bool CLOSED, bool BWD>
+static cudaError_t run_soft_dense_mode(const SoftLaunch& a, cudaStream_t st) {
+  if constexpr (!BWD) {
+    return run_soft_dense<CLOSED, kDenseFwd>(a, st);
+  } else {
+    if (a.fit_target) return run_soft_dense<CLOSED, kDenseFit>(a, st);
+    if (a.ctx_in) return run_soft_dense<CLOSED, kDenseBwdCtx>(a, st);
+    return run_soft_dense<CLOSED, kDenseBwd>(a, st);
+  }
 }
 
 template <bool BWD>
@@ -957,7 +1113,7 @@ static cudaError_t dispatch_soft(const SoftLaunch& a, cudaStream_t st) {
   // search only locates b*
   const bool cl = a.mt.closed != 0;
   if (a.n <= kDenseMax)
-    return cl ? run_soft_dense<true, BWD>(a, st) : run_soft_dense<false, BWD>(a, st);
+    return cl ? run_soft_dense_mode<true, BWD>(a, st) : run_soft_dense_mode<false, BWD>(a, st);
   return cl ? run_soft<5, 4, true, BWD, 16>(a, st) : run_soft<5, 4, false, BWD, 16>(a, st);
 }
 
