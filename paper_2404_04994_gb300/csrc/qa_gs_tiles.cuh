@@ -576,6 +576,12 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
   __syncwarp();
   float* rhi = sht;
   int* rlo = sdot;
+  // int8 maps of 4, 8 or 16 dots with a lane per dot: the team's charges go
+  // out as one 4-, 8- or 16-byte store per pixel (the same for every team of
+  // the launch, so the shuffles below are warp-uniform)
+  const bool vec = !a.out_n16 && (n == 4 || n == 8 || n == 16) && T >= n &&
+                   (reinterpret_cast<uintptr_t>(a.out_n) & (uintptr_t)(n - 1)) == 0;
+  unsigned word = 0u;
   if (active) {
     for (int i = lt; i < n; i += T) {
       int ni = rec->base[i];
@@ -586,7 +592,28 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
       const df ri = df_sub({(float)ni, 0.f}, {rec->chi[i], rec->clo[i]});
       rhi[i] = ri.hi;
       rlo[i] = __float_as_int(ri.lo);
-      store_charge(a, p * n + i, ni, flags);
+      if (vec) {
+        if (ni > 127) { ni = 127; flags |= kFlagOverflow; }
+        word = (unsigned)ni << (8 * (lt & 3));
+      } else {
+        store_charge(a, p * n + i, ni, flags);
+      }
+    }
+  }
+  if (vec) {
+    // bytes of lanes 4q .. 4q + 3 into word q (held by all four), then lane 0
+    // of the team gathers the words and stores them
+    word |= __shfl_xor_sync(kFull, word, 1);
+    word |= __shfl_xor_sync(kFull, word, 2);
+    const int tb = (int)(threadIdx.x & 31u) & ~(T - 1);
+    const unsigned w1 = __shfl_sync(kFull, word, (tb + 4) & 31);
+    const unsigned w2 = __shfl_sync(kFull, word, (tb + 8) & 31);
+    const unsigned w3 = __shfl_sync(kFull, word, (tb + 12) & 31);
+    if (active && lt == 0) {
+      int8_t* dst = a.out_n + p * n;
+      if (n == 16) *reinterpret_cast<int4*>(dst) = make_int4((int)word, (int)w1, (int)w2, (int)w3);
+      else if (n == 8) *reinterpret_cast<int2*>(dst) = make_int2((int)word, (int)w1);
+      else *reinterpret_cast<int*>(dst) = (int)word;
     }
   }
   __syncwarp();
