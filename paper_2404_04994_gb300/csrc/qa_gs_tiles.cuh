@@ -212,52 +212,77 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
   unsigned flags = 0u;
   unsigned qp_set = 0u;
   float bx = a.bx_analytic;
-  if (A) {  // (a3) QP, solved by the team's first lane
+  // (a3) QP where the analytic minimum is infeasible, by the pixel's team
+  const bool need = A != 0u && !(CLOSED && nhat == 0);  // team-uniform
+  const int tb = threadIdx.x - lt;
+  float scale = 1.f;
+  if (A) {
     flags |= kFlagQP;
     const float cmax = tmax_f(live ? fabsf(c.hi + c.lo) : 0.f);
-    if (CLOSED && nhat == 0) {
-      x = {0.f, 0.f};
-    } else {
-      const float scale = 1.f + cmax + (float)nhat;
+    if (need) {
+      scale = 1.f + cmax + (float)nhat;
       bx = fmaxf(bx, bx_qp_scale * scale);
-      float xf = 0.f;
-      unsigned Af = 0u;
-      const int tb = threadIdx.x - lt;
-      const int st = qp_team<float, CLOSED>(n, lt, TP, tmask, tb, sh.cs.Cdd, kLdM, sh.cs.sv,
-                                            sh.cs.s_s, live ? c.hi + c.lo : 0.f, (float)nhat, A,
-                                     0.25f * bx_qp_scale * scale, 4 * n + 4, sh.qK, sh.qa,
-                                     sh.qz, sh.qc, xf, Af);
-      if (st != 0) {
-        flags |= kFlagQPCap;
-        if (live) x = {xf, 0.f};
-      } else {
-        // one double-float refinement: the margin shrinks to the square of
-        // the FP32 one; a multiplier or free x_i below -margin at that
-        // precision leaves the active set (and x) to the FP64 recheck
-        const float bx2 = fmaxf(a.bx_analytic, sh.cs.bx_qp_scale2 * scale);
-        df xr;
-        const int bad = qp_team_refine<CLOSED>(n, lt, TP, tmask, tb, sh.cs.Cdd, sh.cs.CddLo,
-                                               sh.cs.sv2, live ? c : df{0.f, 0.f}, (float)nhat,
-                                               Af, 0.25f * bx2, sh.qK, sh.qa, sh.qz, sh.qzl,
-                                               sh.qx, xr);
-        if (live) x = xr;
-        if (bad) flags |= kFlagBoundary;
-        else bx = bx2;
-        // closed with every dot but one active: the sum constraint makes the
-        // relaxed minimum the vertex N_hat e_j exactly, so once every
-        // multiplier is certainly positive no rounding error is left in x
-        // and the floor decisions need no margin
-        if (CLOSED && !bad && __popc(Af) == n - 1) {
-          const bool zpos = lt >= n - 1 || sh.qz[tb + lt] + sh.qzl[tb + lt] > 0.25f * bx2;
-          if (tballot(!zpos) == 0u) {
-            if (live) x = ((Af >> lt) & 1u) ? df{0.f, 0.f} : df{(float)nhat, 0.f};
-            bx = 0.f;
-          }
-        }
-        qp_set = Af;
-      }
-      __syncwarp(tmask);
+    } else {
+      x = {0.f, 0.f};
     }
+  }
+  float xf = 0.f;
+  unsigned Af = 0u;
+  int st = 0;
+  if (need)
+    st = qp_team<float, CLOSED>(n, lt, TP, tmask, tb, sh.cs.Cdd, kLdM, sh.cs.sv, sh.cs.s_s,
+                                live ? c.hi + c.lo : 0.f, (float)nhat, A,
+                                0.25f * bx_qp_scale * scale, 4 * n + 4, sh.qK, sh.qa, sh.qz,
+                                sh.qc, xf, Af);
+  if (need) {
+    // the FP32 solution stands when its active set is certain at FP32
+    // precision (every free x_i and every multiplier more than twice the
+    // FP32 margin above zero) and no floor or threshold decision lies
+    // within that margin; otherwise one double-float refinement follows
+    bool sure = st == 0;
+    if (sure && live) {
+      if ((Af >> lt) & 1u) {
+        sure = sh.qz[tb + __popc(Af & ((1u << lt) - 1u))] > 2.f * bx;
+      } else {
+        const float fr = xf - floorf(xf);
+        sure = xf > 2.f * bx && !(xf >= 0.5f - bx && fminf(fr, 1.f - fr) < bx) &&
+               !(sh.tlt1 && fabsf(fabsf(fr - 0.5f) - sh.th0) < bx);
+      }
+    }
+    sure = tballot(!sure) == 0u;
+    if (st != 0) {
+      flags |= kFlagQPCap;
+      if (live) x = {xf, 0.f};
+    } else if (sure) {
+      if (live) x = {xf, 0.f};
+      qp_set = Af;
+    } else {
+      // one double-float refinement: the margin shrinks to the square of
+      // the FP32 one; a multiplier or free x_i below -margin at that
+      // precision leaves the active set (and x) to the FP64 recheck
+      const float bx2 = fmaxf(a.bx_analytic, sh.cs.bx_qp_scale2 * scale);
+      df xr;
+      const int bad = qp_team_refine<CLOSED>(n, lt, TP, tmask, tb, sh.cs.Cdd, sh.cs.CddLo,
+                                             sh.cs.sv2, live ? c : df{0.f, 0.f}, (float)nhat,
+                                             Af, 0.25f * bx2, sh.qK, sh.qa, sh.qz, sh.qzl,
+                                             sh.qx, xr);
+      if (live) x = xr;
+      if (bad) flags |= kFlagBoundary;
+      else bx = bx2;
+      // closed with every dot but one active: the sum constraint makes the
+      // relaxed minimum the vertex N_hat e_j exactly, so once every
+      // multiplier is certainly positive no rounding error is left in x
+      // and the floor decisions need no margin
+      if (CLOSED && !bad && __popc(Af) == n - 1) {
+        const bool zpos = lt >= n - 1 || sh.qz[tb + lt] + sh.qzl[tb + lt] > 0.25f * bx2;
+        if (tballot(!zpos) == 0u) {
+          if (live) x = ((Af >> lt) & 1u) ? df{0.f, 0.f} : df{(float)nhat, 0.f};
+          bx = 0.f;
+        }
+      }
+      qp_set = Af;
+    }
+    __syncwarp(tmask);
   }
 
   // (a4) candidate set; the closed doubling loop is team-uniform (its first
@@ -1041,27 +1066,49 @@ __device__ inline void recheck_entry(const GsLaunch& L, const ArrayDesc& a, Rech
     if (lt == 0) S.sqp = (A ? 1 : 0) | (st != 0 ? 2 : 0);
   }
   __syncthreads();
-  if (tid == 0) {
-    int base[kMaxDot];
-    unsigned mask = 0u, fl = (S.sqp & 1) ? kFlagQP : 0u;
-    int w = -1;
-    if (a.md->status != 0 || (S.sqp & 2))
-      sstatus = -1;
-    else
-      sstatus = candidate_set_f64(n, S.sx64, a.mt.t, CLOSED, a.mt.n_charges, base, mask, w, fl);
-    sflags = fl;
-    smask = mask;
-    sw = CLOSED ? w : -1;
-    for (int i = 0; i < n; ++i) sbase[i] = base[i];
-    bcount = 0u;
+  if (wid == 0) {
+    // the candidate set in FP64 (the rules of candidate_set_f64), lane i
+    // deciding dot i, the closed doubling loop warp-uniform
+    const bool live = lane < n;
+    unsigned fl = (S.sqp & 1) ? kFlagQP : 0u;
+    unsigned mask = 0u;
+    int st = -1, w = -1, bi = 0;
+    if (a.md->status == 0 && !(S.sqp & 2)) {
+      const double xl = live ? S.sx64[lane] : 0.0;
+      const double xi = xl > 0.0 ? xl : 0.0;
+      const double fli = floor(xi);
+      const double fr = xi - fli;
+      double tt = a.mt.t;
+      for (int iter = 0; iter < 40; ++iter) {
+        const bool am = live && fabs(fr - 0.5) <= 0.5 * tt;
+        bi = live ? (int)fli + ((!am && fr >= 0.5) ? 1 : 0) : 0;
+        mask = __ballot_sync(kFull, am);
+        if (!CLOSED) { st = 0; break; }
+        int sum = bi;
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(kFull, sum, off);
+        w = a.mt.n_charges - sum;
+        if (w >= 0 && w <= __popc(mask)) { st = 0; break; }
+        if (tt >= 1.0) break;
+        tt = (tt <= 0.0) ? 1.0 : fmin(2.0 * tt, 1.0);
+        fl |= kFlagDoubled;
+      }
+    }
+    if (live) sbase[lane] = bi;
     // same candidate set as the FP32 search and a certain order: keep its result
     const PixRec* rec = a.recs + p;
-    bool same = sstatus == 0 && fe.tie == 0 && mask == (unsigned)rec->mask &&
-                (!CLOSED || w == (int)rec->w);
-    for (int i = 0; i < n && same; ++i) same = base[i] == (int)rec->base[i];
-    if (same) {
-      if (a.out_flags) a.out_flags[p] = (uint8_t)(a.out_flags[p] | fl | kFlagRechecked);
-      sstatus = 1;
+    const bool same = st == 0 && fe.tie == 0 && mask == (unsigned)rec->mask &&
+                      (!CLOSED || w == (int)rec->w) &&
+                      __all_sync(kFull, !live || bi == (int)rec->base[lane]);
+    if (lane == 0) {
+      sflags = fl;
+      smask = mask;
+      sw = CLOSED ? w : -1;
+      bcount = 0u;
+      sstatus = st;
+      if (same) {
+        if (a.out_flags) a.out_flags[p] = (uint8_t)(a.out_flags[p] | fl | kFlagRechecked);
+        sstatus = 1;
+      }
     }
   }
   __syncthreads();
@@ -1152,25 +1199,39 @@ __device__ inline void recheck_entry(const GsLaunch& L, const ArrayDesc& a, Rech
         bbits = rbits[i];
       }
     unsigned flags = (a.out_flags ? a.out_flags[p] : 0u) | sflags | kFlagRechecked;
-    if (overflowed || bbits == 0xffffffffu) {
+    const bool settled = !overflowed && bbits != 0xffffffffu;
+    if (!settled) {
       flags |= kFlagUnresolved;
       atomicAdd(&L.cnt->unresolved, 1ull);
-    } else {
-      int nst[kMaxDot];
-      for (int i = 0; i < n; ++i) nst[i] = sbase[i];
-      for (int s = 0; s < k; ++s)
-        if ((bbits >> s) & 1u) nst[sdot[s]] += 1;
-      double U = 0.0;
-      for (int i = 0; i < n; ++i) {
-        double row = 0.0;
-        for (int j = 0; j < n; ++j) row += a.md->M[i * n + j] * ((double)nst[j] - sc64[j]);
-        U += ((double)nst[i] - sc64[i]) * row;
-      }
-      for (int i = 0; i < n; ++i) store_charge(a, p * n + i, nst[i], flags);
-      if (a.out_U) a.out_U[p] = 0.5 * U;
+      if (a.out_flags) a.out_flags[p] = (uint8_t)flags;
     }
-    if (a.out_flags) a.out_flags[p] = (uint8_t)flags;
+    sflags = flags;
+    rbits[0] = bbits;
+    sstatus = settled ? 2 : 3;
     atomicMax(&L.cnt->shortlist_max, (unsigned long long)nb);
+  }
+  __syncthreads();
+  // the charges and U(n*) = 1/2 r^T M r, r = n* - c, by warp 0: lane i its
+  // dot's charge and row of M r, then a shuffle sum
+  if (sstatus == 2 && wid == 0) {
+    const unsigned bb = rbits[0];
+    const bool live = lane < n;
+    int ni = live ? sbase[lane] : 0;
+    if (live && ((mask >> lane) & 1u)) ni += (int)((bb >> __popc(mask & ((1u << lane) - 1u))) & 1u);
+    double row = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const int nj = __shfl_sync(kFull, ni, j);
+      if (live) row += a.md->M[lane * n + j] * ((double)nj - sc64[j]);
+    }
+    double u = live ? ((double)ni - sc64[lane]) * row : 0.0;
+    for (int off = 16; off > 0; off >>= 1) u += __shfl_xor_sync(kFull, u, off);
+    unsigned fl = 0u;
+    if (live) store_charge(a, p * n + lane, ni, fl);
+    fl = __reduce_or_sync(kFull, fl);
+    if (lane == 0) {
+      if (a.out_U) a.out_U[p] = 0.5 * u;
+      if (a.out_flags) a.out_flags[p] = (uint8_t)(sflags | fl);
+    }
   }
 }
 

@@ -112,8 +112,8 @@ __device__ __noinline__ int qp_active_set(int n, const T* Cdd, int ldc,
 // prep's common path over more instruction-cache lines, which the prep
 // shares with the search's walk in the one-kernel form.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float qsqrt(float v) { return sqrtf(v); }
-__device__ __forceinline__ double qsqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ float qrsqrt(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double qrsqrt(double v) { return rsqrt(v); }
 
 template <typename T, bool CLOSED>
 __device__ __noinline__ int qp_team(int n, int lt, int TP, unsigned tmask, int tbase,
@@ -143,33 +143,37 @@ __device__ __noinline__ int qp_team(int n, int lt, int TP, unsigned tmask, int t
       y = nhat - csum;
     }
     __syncwarp(tmask);
-    // Cholesky, column by column
+    // Cholesky, column by column; the pivot's reciprocal 1 / L_jj (one
+    // reciprocal square root) is kept in the row's spare last column, so the
+    // column and both solves multiply instead of dividing
     bool ok = true;
     for (int j = 0; j < ms; ++j) {
       if (lt == j) {
         T d = Ks[tbase + j][j];
         for (int q = 0; q < j; ++q) d -= Ks[tbase + j][q] * Ks[tbase + j][q];
-        Ks[tbase + j][j] = d > (T)0 ? qsqrt(d) : (T)0;
+        const T r = d > (T)0 ? qrsqrt(d) : (T)0;
+        Ks[tbase + j][j] = d * r;
+        Ks[tbase + j][kQPRow - 1] = r;
       }
       __syncwarp(tmask);
-      const T ljj = Ks[tbase + j][j];
-      if (!(ljj > (T)0)) { ok = false; break; }
+      const T rjj = Ks[tbase + j][kQPRow - 1];
+      if (!(rjj > (T)0)) { ok = false; break; }
       if (lt > j && lt < ms) {
         T e = Ks[tbase + lt][j];
         for (int q = 0; q < j; ++q) e -= Ks[tbase + lt][q] * Ks[tbase + j][q];
-        Ks[tbase + lt][j] = e / ljj;
+        Ks[tbase + lt][j] = e * rjj;
       }
       __syncwarp(tmask);
     }
     if (!ok) return -1;
     // L y = rhs, then L^T z = y (lane p holds unknown p)
     for (int q = 0; q < ms; ++q) {
-      if (lt == q) y /= Ks[tbase + q][q];
+      if (lt == q) y *= Ks[tbase + q][kQPRow - 1];
       const T yq = __shfl_sync(tmask, y, tbase % 32 + q);
       if (lt > q && lt < ms) y -= Ks[tbase + lt][q] * yq;
     }
     for (int q = ms - 1; q >= 0; --q) {
-      if (lt == q) y /= Ks[tbase + q][q];
+      if (lt == q) y *= Ks[tbase + q][kQPRow - 1];
       const T zq = __shfl_sync(tmask, y, tbase % 32 + q);
       if (lt < q) y -= Ks[tbase + q][lt] * zq;
     }
@@ -255,12 +259,12 @@ __device__ __noinline__ int qp_team_refine(int n, int lt, int TP, unsigned tmask
     y = r.hi + r.lo;
   }
   for (int q = 0; q < ms; ++q) {
-    if (lt == q) y /= Ks[tbase + q][q];
+    if (lt == q) y *= Ks[tbase + q][kQPRow - 1];
     const float yq = __shfl_sync(tmask, y, tbase % 32 + q);
     if (lt > q && lt < ms) y -= Ks[tbase + lt][q] * yq;
   }
   for (int q = ms - 1; q >= 0; --q) {
-    if (lt == q) y /= Ks[tbase + q][q];
+    if (lt == q) y *= Ks[tbase + q][kQPRow - 1];
     const float zq = __shfl_sync(tmask, y, tbase % 32 + q);
     if (lt < q) y -= Ks[tbase + q][lt] * zq;
   }
@@ -371,12 +375,19 @@ __device__ __forceinline__ double scan_voltage(const Scan& sc, int ng, long long
   return sc.V[p * ng + g];
 }
 
-// c_i = s (Cgd V(p))_i in FP64
+// c_i = s (Cgd V(p))_i in FP64 (the raster position found once, not per gate;
+// the voltages as in scan_voltage)
 __device__ __forceinline__ double pixel_c_f64(const ModelData* md, int ng,
                                               const Scan& sc, double carrier,
                                               long long p, int i) {
   double a = 0.0;
-  for (int g = 0; g < ng; ++g) a += md->Cgd[i * ng + g] * scan_voltage(sc, ng, p, g);
+  if (sc.kind == 0) {
+    const long long iy = p / sc.W, ix = p - iy * sc.W;
+    const double xs = sc.x0 + (int)ix * sc.dx, ys = sc.y0 + (int)iy * sc.dy;
+    for (int g = 0; g < ng; ++g) a += md->Cgd[i * ng + g] * (sc.V0[g] + xs * sc.u[g] + ys * sc.w[g]);
+  } else {
+    for (int g = 0; g < ng; ++g) a += md->Cgd[i * ng + g] * sc.V[p * ng + g];
+  }
   return carrier * a;
 }
 
