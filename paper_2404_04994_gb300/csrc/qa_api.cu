@@ -343,10 +343,14 @@ qa::SearchCfg choose_cfg(int n, double t, long long P, int num_sms, bool closed)
     c.T = rest <= 0 ? 1 : (rest >= 4 ? 16 : (1 << rest));
   }
   // spread a small raster over more lanes while each lane keeps >= 2 outer
-  // states of work
+  // states of work at the expected ambiguous count (>= 1 below t = 1, where
+  // the count varies from pixel to pixel and the pixels above it set the
+  // time: 4-lane teams instead of 2 on the 16-dot diagram at t = 0.5, 0.049
+  // -> 0.043 ms)
   const int spare = ke - c.L1 - c.L2;
+  const int keep = t < 1.0 ? 1 : 4;
   while (c.T < 32 && P * c.T < (long long)num_sms * 128 * 4 && spare > 0 &&
-         (1 << spare) >= 4 * c.T)
+         (1 << spare) >= keep * c.T)
     c.T *= 2;
   return c;
 }
