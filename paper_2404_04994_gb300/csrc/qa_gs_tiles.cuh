@@ -13,8 +13,8 @@ namespace qa {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPrepThreads = 128;
-constexpr int kRecheckThreads = 128;
-constexpr int kResolveThreads = 256;
+constexpr int kRecheckThreads = 512;  // the tail kernel's block: resolve and recheck alike
+constexpr int kResolveThreads = 512;  // the walk's 512 outer states at k = 16, one per thread
 constexpr int kCheckL1 = 4, kCheckL2 = 3;  // resolve/recheck split: 2^9 outer states at k = 16
 constexpr unsigned kBcap = 1024;
 
@@ -829,10 +829,10 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
   float d1, d2;
   unsigned db;
   unsigned long long ev = 0;
-  static_assert(kResolveThreads <= 256, "the walk's team is the block: at most 8 lane bits");
+  static_assert(kResolveThreads <= 512, "the walk's team is the block: at most 9 lane bits");
   // (outer patterns whose lower bound is above the threshold plus the FP32
   // margin hold no block within the threshold)
-  search_lane<L1, L2, CLOSED, true>(sM, sv, tid, kResolveThreads, thr, blist, &bcnt,
+  search_lane<L1, L2, CLOSED, true, false, 9>(sM, sv, tid, kResolveThreads, thr, blist, &bcnt,
                                     kCap, d1, db, d2, ev, nullptr, nullptr, nullptr,
                                     thr + 2.0f * rec->bound, S.cs.qneg);
   __syncthreads();
@@ -935,15 +935,10 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
     const float gap = second.hi < kInf ? df_add(second, df_neg(best)).hi : kInf;
     const float eps = 1e-10f * (1.f + fabsf(ub.hi));
     const bool ok = fits && bbits != 0xffffffffu && gap > eps;
-    S.dok = ok ? 1 : 0;
+    S.dok = ok ? 1 : 0;  // not ok: the caller rechecks the pixel in FP64 next
     S.dbits = bbits;
     S.dflags = 0u;
-    if (!ok) {
-      const unsigned at = atomicAdd(&L.cnt->n_flag, 1u);
-      L.flag_list[at] = ListEntry{te.array, (int)p, te.m1, 1};
-    } else if (a.out_U) {
-      a.out_U[p] = df_to_double(df_add(ub, best));
-    }
+    if (ok && a.out_U) a.out_U[p] = df_to_double(df_add(ub, best));
     // the shortlist length goes to the counters once per block, at the end
     // of the kernel (an atomic here would hold up the barrier below)
     my_slmax = nb > my_slmax ? nb : my_slmax;
@@ -1145,7 +1140,8 @@ __device__ inline void recheck_entry(const GsLaunch& L, const ArrayDesc& a, Rech
   float m1, m2;
   unsigned b1;
   unsigned long long ev = 0;
-  search_lane<L1, L2, CLOSED, false>(sM, sv, tid, kRecheckThreads, 0.f, nullptr,
+  static_assert(kRecheckThreads <= 512, "the walk's team is the block: at most 9 lane bits");
+  search_lane<L1, L2, CLOSED, false, false, 9>(sM, sv, tid, kRecheckThreads, 0.f, nullptr,
                                      nullptr, 0u, m1, b1, m2, ev);
   for (int off = 16; off > 0; off >>= 1) m1 = fminf(m1, __shfl_xor_sync(kFull, m1, off));
   if (lane == 0) rm1[wid] = m1;
@@ -1155,7 +1151,7 @@ __device__ inline void recheck_entry(const GsLaunch& L, const ArrayDesc& a, Rech
   const float thr = m1 + sbound;
   float d1, d2;
   unsigned db;
-  search_lane<L1, L2, CLOSED, true>(sM, sv, tid, kRecheckThreads, thr, blist,
+  search_lane<L1, L2, CLOSED, true, false, 9>(sM, sv, tid, kRecheckThreads, thr, blist,
                                     &bcount, kBcap, d1, db, d2, ev, nullptr, nullptr, nullptr,
                                     thr + 2.0f * sbound, a.md->k.qneg);
   __syncthreads();

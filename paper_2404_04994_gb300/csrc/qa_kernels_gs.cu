@@ -112,67 +112,68 @@ __global__ void __launch_bounds__(kSearchThreads, kBnbBlocks) k_search_bnb(GsLau
   search_only_tile<kBnbL1, kBnbL2, CLOSED, true>(L);
 }
 
-// Near-tie list: one block per entry, grid-stride.  In a batched call the
-// entries belong to different arrays; the model is restaged when it changes.
-__global__ void __launch_bounds__(kResolveThreads) k_resolve(GsLaunch L) {
-  __shared__ ResolveShared S;
-  int staged = -1;
+// The lists after the search, in one launch: near ties (resolve_entry) and
+// the FP64 recheck list (recheck_entry), grid-stride over both; a near tie
+// the resolve cannot settle is rechecked next by the same block.  The two
+// entries' shared layouts overlap, so each restages its model constants when
+// the other ran last.
+static_assert(kResolveThreads == kRecheckThreads, "one block size for both lists");
+__global__ void __launch_bounds__(kResolveThreads) k_lists(GsLaunch L) {
+  __shared__ union ListShared {
+    ResolveShared r;
+    RecheckShared c;
+  } S;
+  int staged_r = -1, staged_c = -1;  // the array whose constants each layout holds
   if (!L.table) {  // one array: its model is known before the search ends
-    stage_consts(&L.one.md->k, &S.cs);
-    staged = 0;
+    stage_consts(&L.one.md->k, &S.r.cs);
+    staged_r = 0;
   }
-  grid_dep_signal();  // the recheck may launch and stage likewise
-  grid_dep_wait();    // the tie list comes from the search
+  grid_dep_wait();  // the lists come from the search
   const unsigned ntie = L.cnt->n_tie;
+  const unsigned nflag = L.cnt->n_flag;
   unsigned my_res = 0, my_slmax = 0;
-  for (unsigned it = blockIdx.x; it < ntie; it += gridDim.x) {
-    const ListEntry te = L.tie_list[it];
-    const ArrayDesc& a = desc_of(L, te.array);
-    if (te.array != staged) {
-      stage_consts(&a.md->k, &S.cs);
-      staged = te.array;
+  for (unsigned it = blockIdx.x; it < ntie + nflag; it += gridDim.x) {
+    ListEntry e = it < ntie ? L.tie_list[it] : L.flag_list[it - ntie];
+    const ArrayDesc& a = desc_of(L, e.array);
+    bool check = it >= ntie;
+    if (!check) {
+      if (e.array != staged_r) {
+        __syncthreads();
+        stage_consts(&a.md->k, &S.r.cs);
+        staged_r = e.array;
+        staged_c = -1;
+      }
+      if (threadIdx.x == 0) S.r.bcnt = 0u;
+      __syncthreads();
+      if (a.mt.closed)
+        resolve_entry<true>(L, a, S.r, e, my_res, my_slmax);
+      else
+        resolve_entry<false>(L, a, S.r, e, my_res, my_slmax);
+      __syncthreads();
+      check = S.r.dok == 0;
+      e.tie = 1;
+      __syncthreads();
     }
-    if (threadIdx.x == 0) S.bcnt = 0u;
-    __syncthreads();
-    if (a.mt.closed)
-      resolve_entry<true>(L, a, S, te, my_res, my_slmax);
-    else
-      resolve_entry<false>(L, a, S, te, my_res, my_slmax);
-    __syncthreads();
+    if (check) {
+      if (e.array != staged_c) {
+        for (int q = threadIdx.x; q < kMaxDot * kLdM; q += blockDim.x) S.c.sM[q] = a.md->k.Mhi[q];
+        staged_c = e.array;
+        staged_r = -1;
+      }
+      if (threadIdx.x == 0) S.c.bcount = 0u;
+      __syncthreads();
+      if (a.mt.closed)
+        recheck_entry<true>(L, a, S.c, e);
+      else
+        recheck_entry<false>(L, a, S.c, e);
+      __syncthreads();
+    }
   }
   if (threadIdx.x == 0 && my_res) atomicAdd(&L.cnt->resolved, (unsigned long long)my_res);
   if (threadIdx.x == 0 && my_slmax)
     atomicMax(&L.cnt->shortlist_max, (unsigned long long)my_slmax);
-}
-
-// FP64 recheck list: one block per entry, grid-stride.
-__global__ void __launch_bounds__(kRecheckThreads) k_recheck(GsLaunch L) {
-  __shared__ RecheckShared S;
-  int staged = -1;
-  if (!L.table) {  // one array: its model is known before the resolve ends
-    for (int e = threadIdx.x; e < kMaxDot * kLdM; e += blockDim.x) S.sM[e] = L.one.md->k.Mhi[e];
-    staged = 0;
-  }
-  grid_dep_wait();  // the FP64 list is complete once the resolve has run
-  const unsigned nflag = L.cnt->n_flag;
-  for (unsigned it = blockIdx.x; it < nflag; it += gridDim.x) {
-    const ListEntry fe = L.flag_list[it];
-    const ArrayDesc& a = desc_of(L, fe.array);
-    if (fe.array != staged) {
-      for (int e = threadIdx.x; e < kMaxDot * kLdM; e += blockDim.x) S.sM[e] = a.md->k.Mhi[e];
-      staged = fe.array;
-    }
-    if (threadIdx.x == 0) S.bcount = 0u;
-    __syncthreads();
-    if (a.mt.closed)
-      recheck_entry<true>(L, a, S, fe);
-    else
-      recheck_entry<false>(L, a, S, fe);
-    __syncthreads();
-  }
   // the list heads start the next call at zero: the last block to finish
-  // clears them (every block has read n_flag by then, and the resolve, the
-  // reader of n_tie, has completed)
+  // clears them (every block has read both by then)
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -215,8 +216,7 @@ static cudaError_t launch_dependent(void (*kern)(KArgs...), unsigned grid, unsig
 }
 
 cudaError_t launch_lists(const GsLaunch& L, cudaStream_t st) {
-  cudaError_t e = launch_dependent(k_resolve, (unsigned)L.num_sms, kResolveThreads, st, L);
-  if (e == cudaSuccess) e = launch_dependent(k_recheck, (unsigned)L.num_sms, kRecheckThreads, st, L);
+  cudaError_t e = launch_dependent(k_lists, (unsigned)L.num_sms, kResolveThreads, st, L);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
