@@ -262,10 +262,30 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
       // precision leaves the active set (and x) to the FP64 recheck
       const float bx2 = fmaxf(a.bx_analytic, sh.cs.bx_qp_scale2 * scale);
       df xr;
-      const int bad = qp_team_refine<CLOSED>(n, lt, TP, tmask, tb, sh.cs.Cdd, sh.cs.CddLo,
-                                             sh.cs.sv2, live ? c : df{0.f, 0.f}, (float)nhat,
-                                             Af, 0.25f * bx2, sh.qK, sh.qa, sh.qz, sh.qzl,
-                                             sh.qx, xr);
+      unsigned flip = 0u;
+      int bad = qp_team_refine<CLOSED>(n, lt, TP, tmask, tb, sh.cs.Cdd, sh.cs.CddLo, sh.cs.sv2,
+                                       live ? c : df{0.f, 0.f}, (float)nhat, Af, 0.25f * bx2,
+                                       sh.qK, sh.qa, sh.qz, sh.qzl, sh.qx, xr, flip);
+      // a sign violation below FP32 resolution (a nearly degenerate vertex:
+      // a multiplier or free x_i within rounding of zero): one more round
+      // with those constraints toggled -- the FP32 factor and solve of that
+      // active set, and its double-float refinement -- before the FP64
+      // recheck is left to settle the pixel
+      const unsigned A2 = (Af ^ flip) & ((n < 32 ? (1u << n) : 0u) - 1u);
+      if (bad && flip && A2 != Af && !(CLOSED && __popc(A2) == n)) {
+        float xf2 = 0.f;
+        unsigned Af2 = 0u;
+        const int st2 = qp_team<float, CLOSED>(n, lt, TP, tmask, tb, sh.cs.Cdd, kLdM, sh.cs.sv,
+                                               sh.cs.s_s, live ? c.hi + c.lo : 0.f, (float)nhat,
+                                               A2, 0.25f * bx_qp_scale * scale, 1, sh.qK, sh.qa,
+                                               sh.qz, sh.qc, xf2, Af2);
+        if (st2 == 0) {
+          Af = Af2;
+          bad = qp_team_refine<CLOSED>(n, lt, TP, tmask, tb, sh.cs.Cdd, sh.cs.CddLo, sh.cs.sv2,
+                                       live ? c : df{0.f, 0.f}, (float)nhat, Af, 0.25f * bx2,
+                                       sh.qK, sh.qa, sh.qz, sh.qzl, sh.qx, xr, flip);
+        }
+      }
       if (live) x = xr;
       if (bad) flags |= kFlagBoundary;
       else bx = bx2;

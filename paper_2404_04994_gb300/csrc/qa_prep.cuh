@@ -214,14 +214,17 @@ __device__ __noinline__ int qp_team(int n, int lt, int TP, unsigned tmask, int t
 // solved for a correction with the same factor; x is formed again from the
 // corrected multipliers (double-float).  The error of x drops from about
 // cond(Cdd) u to (cond(Cdd) u)^2.  Returns nonzero when, at this precision,
-// a free x_i or a multiplier is below -tol (the active set is then in doubt).
-// Every lane of tmask must call; lane i returns x_i (0 for active dots).
+// a free x_i or a multiplier is below -tol (the active set is then in doubt);
+// `flip` then holds the dots whose constraint that suggests toggling (free
+// dots with x_i < -tol, active dots with a multiplier below -tol).  Every
+// lane of tmask must call; lane i returns x_i (0 for active dots).
 template <bool CLOSED>
 __device__ __noinline__ int qp_team_refine(int n, int lt, int TP, unsigned tmask, int tbase,
                                               const float* CddHi, const float* CddLo,
                                               const df* v2, df ci, float nhat, unsigned A,
                                               float tol, float (*Ks)[kQPRow], const int* alist,
-                                              float* zs, float* zl, float* xr, df& x) {
+                                              float* zs, float* zl, float* xr, df& x,
+                                              unsigned& flip) {
   const bool live = lt < n;
   const int m = __popc(A);
   const int ms = m + (CLOSED ? 1 : 0);
@@ -275,9 +278,12 @@ __device__ __noinline__ int qp_team_refine(int n, int lt, int TP, unsigned tmask
   }
   __syncwarp(tmask);
   xi = act ? df{0.f, 0.f} : form_x(true);
-  const bool bad = (live && !act && xi.hi + xi.lo < -tol) ||
-                   (lt < m && zs[tbase + lt] + zl[tbase + lt] < -tol);
+  const bool xbad = live && !act && xi.hi + xi.lo < -tol;
+  const bool zbad = lt < m && zs[tbase + lt] + zl[tbase + lt] < -tol;
+  const bool bad = xbad || zbad;
   const unsigned anybad = __ballot_sync(tmask, bad) & tmask;
+  flip = __reduce_or_sync(tmask, (xbad ? (1u << lt) : 0u) |
+                                     (zbad ? (1u << alist[tbase + lt]) : 0u));
   __syncwarp(tmask);
   if (xi.hi < 0.f || (xi.hi == 0.f && xi.lo < 0.f)) xi = {0.f, 0.f};
   x = xi;
