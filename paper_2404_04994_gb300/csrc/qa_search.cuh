@@ -697,7 +697,8 @@ __device__ __forceinline__ void team_finish(const float* __restrict__ sM, const 
 // bounds every candidate of o from below.  A closed array's candidates of o
 // set exactly r = w - |o| walked slots (w the candidate weight of Sec. III.B's
 // closed filter), so there the bound is A_o + (the sum of the r smallest
-// L_oj) + qneg, and +inf when no such candidate exists.  An outer pattern whose bound lies
+// lower bounds of the L_oj that hold for every pattern of the lane, sorted
+// once per lane) + qneg, and +inf when no such candidate exists.  An outer pattern whose bound lies
 // above an energy already known to be at least the runner-up (plus the FP32
 // error margin) holds neither the argmin nor the runner-up: it is skipped,
 // and the top two over the candidate set are exactly those over the patterns
@@ -898,6 +899,39 @@ __device__ __forceinline__ void search_bnb(const float* __restrict__ sM, const S
     my[2] = make_float4(cr[0], cr[1], cr[2], cr[3]);
     my[3] = make_float4(cr[4], 0.f, 0.f, 0.f);
   }
+  // closed: the r smallest walked coefficients, bounded once per lane.  A
+  // pattern's coefficient L_oj is the lane part Lt[j] plus the pair terms of
+  // its iteration bits, each at least min(0, M(j, s)), so the sorted lane
+  // parts with those minima added bound the sorted L_oj slot by slot; the sum
+  // of their r smallest is tabulated by the iteration pattern's popcount
+  // (r = w - |o|), +inf where no candidate of that weight exists
+  float rsum[kBnbItBits + 1];
+  if (CLOSED) {
+    const int s0 = kBnbIn + nlb;
+    float c[kBnbIn];
+#pragma unroll
+    for (int j = 0; j < kBnbIn; ++j) {
+      float lo = Lt[j];
+#pragma unroll
+      for (int ii = 0; ii < kBnbItBits; ++ii)
+        lo += (ii < nit) ? fminf(0.f, pm[j * kLdM + min(s0 + ii, kMaxDot - 1)]) : 0.f;
+      c[j] = j < k ? lo : kBig;
+    }
+    bnb_sort7(c);
+    float pre[kBnbIn + 1];
+    pre[0] = 0.f;
+#pragma unroll
+    for (int j = 0; j < kBnbIn; ++j) pre[j + 1] = pre[j] + c[j];
+    const int rmax = min(k, kBnbIn);
+#pragma unroll
+    for (int pc = 0; pc <= kBnbItBits; ++pc) {
+      const int r = w - lpop - pc;
+      float s = kInf;
+#pragma unroll
+      for (int j = 0; j <= kBnbIn; ++j) s = (j == r && r <= rmax) ? pre[j] : s;
+      rsum[pc] = s;
+    }
+  }
   __syncwarp(tmask);
 
   // bounds of the lane's own outer patterns (all 2^kBnbItBits rows are read:
@@ -922,18 +956,8 @@ __device__ __forceinline__ void search_bnb(const float* __restrict__ sM, const S
       const float s3 = fminf(0.f, Lt[6] + i1.w);
       v = (A + ((s0 + s1) + (s2 + s3))) + qneg;
     } else {
-      // the r smallest coefficients of the live walked slots (a sorting
-      // network on seven values; absent slots sort last)
-      float c[kBnbIn] = {Lt[0] + i0.y, Lt[1] + i0.z, Lt[2] + i0.w, Lt[3] + i1.x,
-                         Lt[4] + i1.y, Lt[5] + i1.z, Lt[6] + i1.w};
-#pragma unroll
-      for (int j = 0; j < kBnbIn; ++j) c[j] = j < k ? c[j] : kBig;
-      bnb_sort7(c);
-      const int r = w - (lpop + popc_c((unsigned)i));
-      float sr = 0.f;
-#pragma unroll
-      for (int j = 0; j < kBnbIn; ++j) sr = fmaf(j < r ? 1.f : 0.f, c[j], sr);
-      v = (r < 0 || r > min(k, kBnbIn)) ? kInf : (A + sr) + qneg;
+      (void)i1;
+      v = (A + rsum[popc_c((unsigned)i)]) + qneg;
     }
     // stored rounded down to FP16: still a lower bound, half the space
     if (i < nst) lb[lt | (i << nlb)] = __float2half_rd(v);
