@@ -368,6 +368,9 @@ def extra_measurements(api, torch, flush, args):
         ev = []
         for _ in range(reps):
             flush.zero_()
+            # keep the device busy (about 0.2 ms) while the host marshals the
+            # call, so the events time the device work and not the binding
+            torch.cuda._sleep(400000)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record()

@@ -918,14 +918,16 @@ __device__ inline void resolve_entry(const GsLaunch& L, const ArrayDesc& a, Reso
     second = less(lose, s2) ? lose : s2;
     if (take) { best = ob; bbits = obb; }
   };
-#pragma unroll 1
-  for (int off = 16; off > 0; off >>= 1) {
+  // only the group leaders (sub = 0: lanes 0 and 16) hold candidates, so
+  // one exchange merges a warp
+  static_assert(kMaxDot == 16, "two candidate groups of kMaxDot threads per warp");
+  {
     df ob, os;
-    ob.hi = __shfl_xor_sync(kFull, best.hi, off);
-    ob.lo = __shfl_xor_sync(kFull, best.lo, off);
-    os.hi = __shfl_xor_sync(kFull, second.hi, off);
-    os.lo = __shfl_xor_sync(kFull, second.lo, off);
-    merge(ob, os, __shfl_xor_sync(kFull, bbits, off));
+    ob.hi = __shfl_xor_sync(kFull, best.hi, 16);
+    ob.lo = __shfl_xor_sync(kFull, best.lo, 16);
+    os.hi = __shfl_xor_sync(kFull, second.hi, 16);
+    os.lo = __shfl_xor_sync(kFull, second.lo, 16);
+    merge(ob, os, __shfl_xor_sync(kFull, bbits, 16));
   }
   if (lane == 0) { rbest[wid] = best; rsec[wid] = second; rbits[wid] = bbits; }
   __syncthreads();

@@ -129,11 +129,19 @@ __global__ void __launch_bounds__(kResolveThreads) k_lists(GsLaunch L) {
     staged_r = 0;
   }
   grid_dep_wait();  // the lists come from the search
+  // one array: the block's first near-tie entry is read together with the
+  // list heads instead of after them (the list has room for P entries, so
+  // the index lies inside it; the entry is used only below the head)
+  const bool pf = !L.table && (long long)blockIdx.x < L.one.sc.P;
+  ListEntry first{};
+  if (pf) first = L.tie_list[blockIdx.x];
   const unsigned ntie = L.cnt->n_tie;
   const unsigned nflag = L.cnt->n_flag;
   unsigned my_res = 0, my_slmax = 0;
   for (unsigned it = blockIdx.x; it < ntie + nflag; it += gridDim.x) {
-    ListEntry e = it < ntie ? L.tie_list[it] : L.flag_list[it - ntie];
+    ListEntry e = (pf && it == blockIdx.x && it < ntie)
+                      ? first
+                      : (it < ntie ? L.tie_list[it] : L.flag_list[it - ntie]);
     const ArrayDesc& a = desc_of(L, e.array);
     bool check = it >= ntie;
     if (!check) {
