@@ -627,21 +627,40 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
   const bool vec = !a.out_n16 && (n == 4 || n == 8 || n == 16) && T >= n &&
                    (reinterpret_cast<uintptr_t>(a.out_n) & (uintptr_t)(n - 1)) == 0;
   unsigned word = 0u;
+  // the record's flags and bound, and the lane's dots' base and c, four dots
+  // at a time: their loads are issued together (one round trip to L2)
+  const unsigned rflags = active ? rec->flags : 0u;
+  const float rbound = active ? rec->bound : 0.f;
   if (active) {
-    for (int i = lt; i < n; i += T) {
-      int ni = rec->base[i];
-      if ((mask >> i) & 1u) {
-        const int si = BNB ? slot_of[i] : __popc(mask & ((1u << i) - 1u));
-        ni += (int)((b1 >> si) & 1u);
+    for (int i0 = lt; i0 < n; i0 += 4 * T) {
+      int bq[4];
+      float chq[4], clq[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + q * T;
+        const int ic = i < n ? i : i0;
+        bq[q] = rec->base[ic];
+        chq[q] = rec->chi[ic];
+        clq[q] = rec->clo[ic];
       }
-      const df ri = df_sub({(float)ni, 0.f}, {rec->chi[i], rec->clo[i]});
-      rhi[i] = ri.hi;
-      rlo[i] = __float_as_int(ri.lo);
-      if (vec) {
-        if (ni > 127) { ni = 127; flags |= kFlagOverflow; }
-        word = (unsigned)ni << (8 * (lt & 3));
-      } else {
-        store_charge(a, p * n + i, ni, flags);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + q * T;
+        if (i >= n) continue;
+        int ni = bq[q];
+        if ((mask >> i) & 1u) {
+          const int si = BNB ? slot_of[i] : __popc(mask & ((1u << i) - 1u));
+          ni += (int)((b1 >> si) & 1u);
+        }
+        const df ri = df_sub({(float)ni, 0.f}, {chq[q], clq[q]});
+        rhi[i] = ri.hi;
+        rlo[i] = __float_as_int(ri.lo);
+        if (vec) {
+          if (ni > 127) { ni = 127; flags |= kFlagOverflow; }
+          word = (unsigned)ni << (8 * (lt & 3));
+        } else {
+          store_charge(a, p * n + i, ni, flags);
+        }
       }
     }
   }
@@ -662,7 +681,16 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
     }
   }
   __syncwarp();
-  if (active) {
+  // U = r^T M r.  The pruned search's wide teams (a row per lane) sum full
+  // rows, M_ij r_j over j, scaled by r_i.  Narrower teams, whose lanes take
+  // several rows each, use the symmetry: U = sum_i r_i S_i with
+  // S_i = M_ii r_i + 2 sum_{j > i} M_ij r_j (the upper triangle, 136 products
+  // at N = 16 instead of 256); rows i and N - 1 - i pair up to N + 1
+  // products, one pair per task, or half a pair when the team has lanes for
+  // that; a task's part of each row is summed, scaled by r_i and added to
+  // the lane's u.  (Measured: the shorter sums do not pay at 16 lanes, where
+  // the pair tasks' extra code costs more than the products they save.)
+  if (active && BNB) {
     const int nc = T >= 2 * n ? T / n : 1;
     const int cw = (n + nc - 1) / nc;
     for (int task = lt; task < n * nc; task += T) {
@@ -680,6 +708,48 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
       const df acc = fast_two_sum(shi, slo);
       u = df_add(u, df_mul(acc, {rhi[i], __int_as_float(rlo[i])}));
     }
+  } else if (active) {
+    const int npair = (n + 1) >> 1;
+    const int nt = T >= 2 * npair ? 2 : 1;
+    for (int task = lt; task < npair * nt; task += T) {
+      const int pp = task / nt, hh = task - pp * nt;
+      const int q = n - 1 - pp;
+      const int len1 = n - pp, len = len1 + (q != pp ? pp + 1 : 0);
+      const int mid = (len + 1) >> 1;
+      const int e0 = (nt == 2 && hh) ? mid : 0;
+      const int e1 = (nt == 2 && !hh) ? mid : len;
+      for (int seg = 0; seg < 2; ++seg) {
+        const int i = seg ? q : pp;
+        const int sa = seg ? max(e0 - len1, 0) : e0;
+        const int sb = seg ? e1 - len1 : min(e1, len1);
+        if (sb <= sa) continue;
+        const int ja = i + sa, jb = i + sb;
+        // four columns per step with their loads issued together and two
+        // independent sums (even and odd columns), joined error-free at the
+        // end; a column past the range adds exact zeros, the off-diagonal
+        // ones count twice (an exact scaling)
+        float shi[2] = {0.f, 0.f}, slo[2] = {0.f, 0.f};
+        for (int jb4 = ja; jb4 < jb; jb4 += 4) {
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const int j = jb4 + jj;
+            const bool on = j < jb;
+            const int jc = on ? j : ja;
+            const float wt = !on ? 0.f : (j == i ? 1.f : 2.f);
+            const float mh = wt * sM[i * kLdM + jc], ml = wt * sMlo[i * kLdM + jc];
+            const float xh = rhi[jc], xl = __int_as_float(rlo[jc]);
+            const df pr = two_prod(mh, xh);
+            const float small = __fmaf_rn(mh, xl, __fmaf_rn(ml, xh, pr.lo));
+            const df sm = two_sum(shi[jj & 1], pr.hi);
+            shi[jj & 1] = sm.hi;
+            slo[jj & 1] = __fadd_rn(slo[jj & 1], __fadd_rn(sm.lo, small));
+          }
+        }
+        const df st = two_sum(shi[0], shi[1]);
+        const df acc = two_sum(st.hi, __fadd_rn(st.lo, __fadd_rn(slo[0], slo[1])));
+        u = df_add(u, df_mul(acc, {rhi[i], __int_as_float(rlo[i])}));
+      }
+    }
   }
   for (int off = 1; off < T; off <<= 1) {
     df o;
@@ -690,8 +760,8 @@ __device__ inline void search_tile(const GsLaunch& L, const ArrayDesc& a, Search
   }
   unsigned my_nt = 0, my_bd = 0, my_ov = 0;
   if (active) {
-    flags |= rec->flags;
-    if (!(m2 - m1 > rec->bound)) flags |= kFlagNearTie;
+    flags |= rflags;
+    if (!(m2 - m1 > rbound)) flags |= kFlagNearTie;
     if (lt == 0) {
       if (a.out_U) a.out_U[p] = 0.5 * df_to_double(u);
       if (flags & (kFlagBoundary | kFlagQPCap | kFlagUnresolved)) {
