@@ -321,7 +321,12 @@ int select_device(const qa_model* m) {
 
 qa::SearchCfg choose_cfg(int n, double t, long long P, int num_sms, bool closed) {
   const double kexp = (t >= 1.0) ? (double)n : (double)n * std::log2(1.0 + t);
-  const int ke = (int)std::ceil(kexp - 1e-9);
+  // closed arrays below t = 1 double t for the pixels whose candidate set
+  // misses the total charge, and those pixels can reach every dot ambiguous:
+  // they get a split whose outer states cover 2^9 candidates (the 16-dot
+  // diagram at t = 0 took 2.4 ms with the 4 + 0 split the expected count picks)
+  const int ke0 = (int)std::ceil(kexp - 1e-9);
+  const int ke = (closed && t < 1.0) ? std::max(ke0, std::min(n, 10)) : ke0;
   qa::SearchCfg c;
   if (n <= 2) c = {2, 0, 1};
   else if (ke <= 4) c = {4, 0, 1};
@@ -342,6 +347,12 @@ qa::SearchCfg choose_cfg(int n, double t, long long P, int num_sms, bool closed)
     // rasters are widened below
     c.T = rest <= 0 ? 1 : (rest >= 4 ? 16 : (1 << rest));
   }
+  // small rasters of many dots: a pixel's slot tables, finish and energy are
+  // spread over its team's lanes, so four lanes at least even where the walk
+  // leaves some of them idle (16-dot 100 x 100 diagram at t = 0.25, split
+  // 4 + 3: 1, 2, 4, 16 lanes 105, 48, 36, 39 us; at t = 0.5 four lanes are
+  // the widening below anyway)
+  if (n >= 12 && c.T < 4 && P * 4 < (long long)num_sms * 128 * 4) c.T = 4;
   // spread a small raster over more lanes while each lane keeps >= 2 outer
   // states of work at the expected ambiguous count (>= 1 below t = 1, where
   // the count varies from pixel to pixel and the pixels above it set the
