@@ -229,7 +229,37 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
   float xf = 0.f;
   unsigned Af = 0u;
   int st = 0;
-  if (need)
+  // open array with one negative c_a (every QP pixel of the 16-dot diagram):
+  // the active set {a} solved in place -- z_a = -c_a / Cdd_aa through the
+  // same reciprocal square root, x_i = c_i + Cdd_ia z_a -- with the same
+  // operations, results and shared state (factor, active list, multiplier)
+  // as the team QP's first iteration; it stands when no other x_i is below
+  // -tol, else the team QP runs from {a}
+  bool solved = false;
+  if (!CLOSED && need && __popc(A) == 1) {
+    const int ad = __ffs(A) - 1;
+    const float cl = live ? c.hi + c.lo : 0.f;
+    const float ca = __shfl_sync(tmask, cl, ad, TP);
+    const float caa = sh.cs.Cdd[ad * kLdM + ad];
+    const float r = caa > 0.f ? rsqrtf(caa) : 0.f;
+    const float zf = (-ca * r) * r;
+    float xi = 0.f;
+    if (live && lt != ad) xi = cl + sh.cs.Cdd[lt * kLdM + ad] * zf;
+    const float tolq = 0.25f * bx_qp_scale * scale;
+    solved = r > 0.f && tballot(live && lt != ad && xi < -tolq) == 0u;
+    if (solved) {
+      if (lt == 0) {
+        sh.qa[tb] = ad;
+        sh.qz[tb] = zf;
+        sh.qK[tb][0] = caa * r;
+        sh.qK[tb][kQPRow - 1] = r;
+      }
+      xf = (live && lt != ad) ? (xi > 0.f ? xi : 0.f) : 0.f;
+      Af = A;
+      __syncwarp(tmask);
+    }
+  }
+  if (need && !solved)
     st = qp_team<float, CLOSED>(n, lt, TP, tmask, tb, sh.cs.Cdd, kLdM, sh.cs.sv, sh.cs.s_s,
                                 live ? c.hi + c.lo : 0.f, (float)nhat, A,
                                 0.25f * bx_qp_scale * scale, 4 * n + 4, sh.qK, sh.qa, sh.qz,
