@@ -86,10 +86,14 @@ __device__ __forceinline__ U block_sum(U v, U* red) {
 // ---------------------------------------------------------------------------
 // prep stage: shared state of a block and the per-array set-up
 // ---------------------------------------------------------------------------
+// Point lists with at most this many gates take c from a staged s Cgd and
+// voltages converted once per pixel by the team (one gate per lane).
+constexpr int kPointGates = 16;
 struct PrepShared {
   ModelConsts cs;
   df sV[kMaxGate], sU[kMaxGate], sW[kMaxGate];
   df sc0[kMaxDot], sdu[kMaxDot], sdw[kMaxDot];
+  df sG[kMaxDot][kPointGates];     // point lists of <= kPointGates gates: s Cgd
   float qK[kPrepThreads][kQPRow];  // team QP: KKT rows, active lists, unknowns, c
   int qa[kPrepThreads];
   float qz[kPrepThreads];
@@ -110,6 +114,12 @@ __device__ inline void prep_stage_array(const ArrayDesc& a, PrepShared& sh) {
     sh.th0 = __double2float_rn(0.5 * a.mt.t);
     sh.tlt1 = a.mt.t < 1.0 ? 1 : 0;
   }
+  if (a.sc.kind == 1 && a.ng <= kPointGates && a.prep_team >= a.ng) {
+    for (int e = threadIdx.x; e < a.n * a.ng; e += blockDim.x) {
+      const int i = e / a.ng, g = e - i * a.ng;
+      sh.sG[i][g] = df_from_double(a.mt.carrier * a.md->Cgd[i * a.ng + g]);
+    }
+  }
   if (a.sc.kind == 0) {
     if (a.rk.valid) {
       if (threadIdx.x < kMaxDot) {
@@ -123,6 +133,28 @@ __device__ inline void prep_stage_array(const ArrayDesc& a, PrepShared& sh) {
     }
   }
   __syncthreads();
+}
+
+// c of a point-list pixel by its team (out of line: the raster kernels carry
+// only the call): lane g converts V_g to double-float once for the team,
+// through the team's scratch rows, and each live lane sums its dot's row of
+// the staged s Cgd, the same operations in the same order as point_c.
+// Every lane of tmask must call; ng <= the team's lanes.
+static __device__ __noinline__ df point_c_team(const double* Vp, int ng, bool active, bool live,
+                                               int lt, unsigned tmask,
+                                               const df (*sG)[kPointGates], float* qx,
+                                               float* qz) {
+  const int tq = (int)threadIdx.x - lt;
+  df vg = {0.f, 0.f};
+  if (active && lt < ng) vg = df_from_double(Vp[lt]);
+  qx[threadIdx.x] = vg.hi;
+  qz[threadIdx.x] = vg.lo;
+  __syncwarp(tmask);
+  df acc = {0.f, 0.f};
+  if (live)
+    for (int g = 0; g < ng; ++g) acc = df_add(acc, df_mul(sG[lt][g], df{qx[tq + g], qz[tq + g]}));
+  __syncwarp(tmask);
+  return acc;
 }
 
 // Per-block totals of the prep stage (thread 0's copy is the block's).
@@ -182,9 +214,16 @@ __device__ inline void prep_tile(const ArrayDesc& a, PrepShared& sh, long long t
   };
   auto tballot = [&](bool pred) { return (__ballot_sync(tmask, pred) & tmask) >> tbase; };
 
-  // (a1) c_i
+  // (a1) c_i; a point list of at most one gate per lane: lane g converts the
+  // pixel's V_g to double-float once for the team (the team's scratch rows),
+  // then each lane sums its dot's row of the staged s Cgd -- the same
+  // operations in the same order as point_c, without the per-lane FP64
+  // conversions
   df c = {0.f, 0.f};
-  if (live) {
+  if (a.sc.kind == 1 && a.ng <= kPointGates && TP >= a.ng) {
+    c = point_c_team(a.sc.V + (active ? p : 0) * a.ng, a.ng, active, live, lt, tmask, sh.sG,
+                     sh.qx, sh.qz);
+  } else if (live) {
     if (a.sc.kind == 0) {
       int ix, iy;
       if (a.sc.P <= 0xffffffffLL) {  // 32-bit division when the raster allows it
