@@ -346,8 +346,9 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": world * P / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo)},
-            # per step: k_ground_state (prep + search), k_resolve, k_recheck
-            "gpu_launches": 3 * args.steps, "clocks": clk, "extra": extra}
+            # per step: k_ground_state_bnb (prep + pruned search of each
+            # tile) and k_lists (near-tie resolve and FP64 recheck)
+            "gpu_launches": 2 * args.steps, "clocks": clk, "extra": extra}
     if rank == 0:
         print(json.dumps(line))
     m.close()
