@@ -393,7 +393,7 @@ int qa_batch_create(const qa_batch_item* items, int count, qa_batch** out);
 
 /* Run the batch on `stream`: one persistent prep launch and one persistent
  * search launch whose blocks take work units from a device queue, then the
- * near-tie and FP64 recheck kernels over all arrays.  Asynchronous, allocates
+ * list kernel (near-tie resolve, FP64 recheck) over all arrays.  Asynchronous, allocates
  * nothing and synchronises nothing, so it can be captured in a CUDA graph.
  * Runs of one batch must not overlap on the GPU. */
 int qa_batch_run(qa_batch* b, void* stream);

@@ -9,7 +9,7 @@
 // h = M (base - c) are formed in double-float FP32 arithmetic (error-free
 // transformations, Dekker 1971 / Knuth TAOCP Vol. 2 4.2.2); candidate energies
 // are summed in plain FP32 with a per-pixel error bound; pixels whose decisions
-// fall inside the bound are re-evaluated in FP64 by the recheck kernel.
+// fall inside the bound are re-evaluated in FP64 by the list kernel.
 #pragma once
 
 #include <cstddef>
@@ -158,13 +158,13 @@ struct Counters {
   unsigned int q_prep;  // batched launch: work-queue heads
   unsigned int q_search;
   unsigned int q_var[20];  // batched launch: the search queue of each kernel variant
-  unsigned int lists_done; // blocks of the FP64 recheck kernel that have finished
+  unsigned int lists_done; // blocks of the list kernel that have finished
   unsigned int soft_done;  // blocks of the soft gradient reduction that have finished
 };
 
 // A single-array call's first kernel clears every counter but the two list
 // heads, which its own blocks append to while others are still starting; the
-// last block of the call's FP64 recheck kernel clears those (and lists_done)
+// last block of the call's list kernel clears those (and lists_done)
 // instead, so the heads are zero whenever a call starts.
 __device__ __forceinline__ void zero_accumulators(Counters* c) {
   constexpr int nw = (int)(sizeof(Counters) / sizeof(unsigned));

@@ -66,7 +66,7 @@ struct GsLaunch {
   const WorkUnit* search_units;
   int n_search_units;
   ListEntry* flag_list;        // scratch: pixels for the FP64 recheck
-  ListEntry* tie_list;         // scratch: near-tie pixels for the resolve kernel
+  ListEntry* tie_list;         // scratch: near-tie pixels for the list kernel's resolve
   Counters* cnt;               // scratch; list heads zero at the start of each call
   BlockCounts* bc_prep;        // scratch [prep blocks]
   BlockCounts* bc_search;      // scratch [search blocks]
